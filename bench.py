@@ -1,0 +1,326 @@
+"""Benchmark of the massive PRNG hot path on GB300.
+
+Workload (default): the paper-shaped streaming run -- 2^22 streams x 1024
+iterations, seed 12345, uint64 output in the iteration-major layout (32 GiB
+per step).  One step = rng_init + rng_generate over the whole workload.
+
+* ``value``: device-resident generation, GB/s of uint64 output (8 bytes per
+  value), the output written into a 32 GiB device buffer (larger than L2, so
+  no flush is needed between steps), timed with CUDA events on the
+  generator's compute stream.
+* ``e2e``: the same step through the C ABI with a host output buffer
+  (page-locked, 32 GiB): values are generated into two 32 MiB device
+  buffers and copied to the host on a copy stream while the next buffer is
+  generated; the timed region includes every device-to-host byte.
+* ``roofline``: the row kernel's average launch time from the library's own
+  CUDA events (recorded on the stream it launches on) over the timed region.
+* ``cpu_baseline``: the CPU oracle timed on a bounded sample on rank 0.
+
+``--impl reference`` times the CPU oracle instead (the method's plain
+definition, single-threaded) on a bounded sample of the same workload.
+Under torchrun every rank generates its own block of 2^22 stream ids (weak
+scaling, no data exchange); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+GIB = 1 << 30
+
+WORKLOADS = {
+    "streaming": dict(streams=1 << 22, iterations=1024, seed=12345, device_buffer_bytes=32 << 20,
+                      name="paper-shaped streaming run: 2^22 streams x 1024 iterations, seed 12345"),
+    "plain": dict(streams=1 << 16, iterations=100, seed=0, device_buffer_bytes=32 << 20,
+                  name="plain method: 2^16 streams x 100 iterations, seed 0"),
+}
+
+METRIC = "GB/s of uint64 PRNG output (device and host-streamed) vs roofline; p50/p99 req latency"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rows_kernel_traffic.md")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return rank, ws
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "prng_math.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1609_01257_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch(workload: str):
+    """DRAM bytes per launch of the row kernel from the committed ncu summary,
+    when it was taken on the current kernel source; else None."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m = re.search(rf"traffic_bytes_per_launch\[{workload}\]:\s*([0-9.eE+]+)", txt)
+    if not m or not m_hash or m_hash.group(1) != _kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_oracle_sample(streams: int, seed: int, iterations: int):
+    """Times the CPU oracle (single thread) on `iterations` rows of the workload."""
+    sys.path.insert(0, ROOT)
+    import oracle  # test infrastructure: the CPU baseline leg only
+    oracle.build()
+    t0 = time.perf_counter()
+    out = oracle.generate(streams, seed, iterations)
+    dt = time.perf_counter() - t0
+    return out.nbytes, dt
+
+
+def run_reference(args, wl):
+    rank, ws = _dist()
+    if rank != 0:
+        return 0
+    # Bounded sample per step: all streams, first `rows` iterations.
+    rows = args.reference_rows
+    times, nbytes = [], 0
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl["streams"], wl["seed"], rows)
+    for _ in range(args.steps):
+        nbytes, dt = cpu_oracle_sample(wl["streams"], wl["seed"], rows)
+        times.append(dt)
+    total = sum(times)
+    gbs = nbytes * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "streams": wl["streams"], "iterations": wl["iterations"],
+                   "seed": wl["seed"], "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{wl['streams']} streams x first {rows} iterations per step"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
+    nbytes = 8 * n * T
+    gen = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+                        init=False)
+    stream = gen.stream
+    out = torch.empty((T, n), dtype=torch.uint64, device="cuda")
+    torch.cuda.synchronize()
+
+    def step_device():
+        gen.init()
+        gen.generate_to(T, out.data_ptr())
+
+    # ---- device-resident leg ------------------------------------------------
+    for _ in range(args.warmup):
+        step_device()
+    gen.sync()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    gen.profile_reset()
+    launches0 = rng.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_device()
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = rng.launch_count() - launches0
+    dev_s = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+    k_count, k_total = gen.profile_stat("RNG_KERNEL")
+    k_avg = max_over_ranks(k_total / max(k_count, 1))
+    value = nbytes * ws * args.steps / dev_s / 1e9
+    vpt, block, grid = gen.launch_config()
+    del out
+    torch.cuda.empty_cache()
+
+    # ---- end-to-end leg: host output through the C ABI ------------------------
+    e2e = None
+    if not args.skip_e2e:
+        host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
+
+        def step_host():
+            gen.init()
+            gen.generate_to_host(T, host)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            step_host()
+        barrier()
+        gen.profile_reset()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_host()
+        barrier()
+        host_s = max_over_ranks(time.perf_counter() - t0)
+        prof = gen.profile()
+        e2e = {"value": nbytes * ws * args.e2e_steps / host_s / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes,
+               "steps": args.e2e_steps, "ms_per_step": 1e3 * host_s / args.e2e_steps,
+               "read_buffer_s": prof["aggregate"].get("READ_BUFFER", (0, 0))[0] / args.e2e_steps,
+               "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0] / args.e2e_steps,
+               "overlap_s": sum(prof["overlaps"].values()) / args.e2e_steps}
+        del host
+
+    gen.close()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, src = _peaks()
+    achieved = nbytes / k_avg / 1e9
+    traffic = _traffic_per_launch(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl["name"], "streams_per_gpu": n, "iterations": T, "seed": seed,
+                   "bytes_per_step_per_gpu": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
+                   "l2": "output 32 GiB per step > 129 MB L2: no flush needed",
+                   "parallelism": f"dp{ws} (disjoint stream-id blocks)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": f"{src}: hbm_gbs (copy, read+write) from MEASURED_PEAKS.json",
+                     "kernel": "rows_kernel", "kernel_avg_ms": k_avg * 1e3, "launches": k_count},
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if not args.skip_cpu_baseline and ws == 1:
+        rows = args.cpu_rows
+        nb, dt = cpu_oracle_sample(n, seed, rows)
+        line["cpu_baseline"] = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n} streams x first {rows} iterations ({nb / GIB:.1f} GiB), "
+                                          f"single-threaded C oracle, {dt:.1f} s"}
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="streaming")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=128, help="iterations in the CPU-baseline sample")
+    ap.add_argument("--reference-rows", type=int, default=16, help="iterations per reference step")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

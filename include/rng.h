@@ -1,0 +1,277 @@
+/*
+ * rng.h -- C ABI of the GB300 massive pseudo-random number generator.
+ *
+ * The generator is the example application of the cf4ocl paper (Fachada,
+ * Lopes, Martins, Rosa, "cf4ocl: a C framework for OpenCL", Section 5,
+ * "Example: massive pseudo-random number generator", kernels in Listings
+ * S4 and S5).  n streams ("work-items") each hold a 64-bit state.  The
+ * initial state of stream g is a hash of its 32-bit id (Listing S4) and is
+ * also the stream's first output; every later output is the previous state
+ * advanced by the xorshift update s ^= s << 21; s ^= s >> 35; s ^= s << 4
+ * (Listing S5).  One call produces i iterations of n values in the
+ * iteration-major layout of Section 5: value[it * n + g], 8 * n * i bytes
+ * in total (Eq. 1).
+ *
+ * Run seed (the paper has none): the 32-bit id is XORed with
+ * key(seed) = lo32(mix64(seed)) ^ hi32(mix64(seed)) before hashing, mix64
+ * being the splitmix64 output finaliser.  key(0) = 0, so seed 0 gives the
+ * paper's numbers exactly.
+ *
+ * Conventions (Section 3.1 of the paper):
+ *  - every constructor (*_create, *_new) has a matching destructor;
+ *    destructors accept NULL; rng_live_objects() counts live objects;
+ *  - an error is reported twice: as the return value (an rng_status code)
+ *    and, when the caller passes a non-NULL `rng_err **err` whose *err is
+ *    NULL, as a newly allocated rng_err that the caller frees with
+ *    rng_err_clear().  An *err that is already set is left as it is.
+ *  - no function calls exit() or aborts the process.
+ *  - strings returned by the library are owned by the object they came from
+ *    and stay valid until the next call on that object or its destruction.
+ */
+#ifndef PRNG_GB300_RNG_H
+#define PRNG_GB300_RNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Errors                                                              */
+/* ------------------------------------------------------------------ */
+enum rng_status {
+    RNG_OK = 0,
+    RNG_EINVAL = 1,   /* bad argument (NULL object, size out of range, ...) */
+    RNG_ENOMEM = 2,   /* device or pinned host allocation failed */
+    RNG_ECUDA = 3,    /* a CUDA runtime call failed; message names it */
+    RNG_ESTATE = 4,   /* call out of order (e.g. generate before init) */
+    RNG_ETIMEOUT = 5, /* a bounded wait gave up */
+    RNG_EBUDGET = 6,  /* request does not fit the memory budget */
+    RNG_ESINK = 7     /* a host consumer callback returned non-zero */
+};
+
+typedef struct rng_err {
+    int code;       /* one of rng_status */
+    char msg[256];  /* human-readable description */
+} rng_err;
+
+/* Frees *err (if any) and sets it to NULL.  NULL-safe. */
+void rng_err_clear(rng_err **err);
+/* Static string naming a status code. */
+const char *rng_strerror(int code);
+/* Number of library objects (generators, profilers, batches, servers)
+ * created and not yet destroyed -- the memcheck of Section 3.1. */
+long rng_live_objects(void);
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t rng_launch_count(void);
+
+/* ------------------------------------------------------------------ */
+/* Options                                                             */
+/* ------------------------------------------------------------------ */
+typedef struct rng_opts {
+    uint32_t struct_size;         /* sizeof(rng_opts), set by rng_opts_default */
+    uint32_t values_per_thread;   /* streams per GPU thread: 1,2,4,...,64; 0 = choose */
+    uint32_t block_threads;       /* threads per block: 128, 256 or 512; 0 = 256 */
+    uint32_t fuse_init;           /* 1 (default): rng_init launches nothing and the
+                                     first rng_generate hashes the ids itself;
+                                     0: rng_init runs the separate init kernel */
+    uint64_t stream_offset;       /* id of this object's first stream (a shard of
+                                     a larger generator); ids g0 .. g0+n-1 */
+    uint64_t device_buffer_bytes; /* host output: size of each of the two device
+                                     buffers (ping-pong, Section 5); default 32 MiB */
+    uint32_t host_slots;          /* pinned staging slots for pageable host output
+                                     and for sinks; default 2 */
+    uint32_t profiling;           /* 1 (default): time every kernel and copy with
+                                     CUDA events for the profiler */
+    void *compute_stream;         /* cudaStream_t for kernels; NULL = own stream */
+    int32_t device;               /* CUDA device ordinal; -1 = current device */
+    uint32_t store_policy;        /* 0 = default stores, 1 = streaming (.cs) */
+    uint32_t host_wait_ms;        /* longest wait for a free staging slot while a
+                                     host consumer holds them all; 0 = 600000 */
+} rng_opts;
+
+void rng_opts_default(rng_opts *opts);
+
+/* ------------------------------------------------------------------ */
+/* Generator (Section 5: init kernel, rng kernel, device->host reads)  */
+/* ------------------------------------------------------------------ */
+typedef struct rng_gen rng_gen;
+
+/* Creates a generator of `streams` streams (1 <= streams <= 2^32; ids
+ * are reduced to 32 bits before hashing, as in Listing S4) with run seed
+ * `seed`.  Allocates the state array (8 bytes per stream) on the device.
+ * `opts` may be NULL (defaults).  The generator must be initialised with
+ * rng_init before the first rng_generate. */
+int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts,
+               rng_gen **out, rng_err **err);
+
+/* Section 5, init kernel (Listing S4): state of stream g := hash of
+ * (g0 + g) and the seed; position := 0.  Ordered on the compute stream;
+ * returns before the device work completes.  Calling it again restarts
+ * the streams. */
+int rng_init(rng_gen *g, rng_err **err);
+
+/* Section 5, rng kernel (Listing S5) plus the device-side double buffer:
+ * emits iterations p .. p+iterations-1 (p = current position, iteration 0
+ * being the init value) and then advances p by `iterations`.
+ * Exactly one of the two outputs is non-NULL:
+ *  - out_dev: caller-owned device memory of at least 8*streams*iterations
+ *    bytes, 8-byte aligned (16-byte alignment enables vector stores);
+ *    value (it - p) * streams + g.  Ordered on the compute stream; returns
+ *    before the kernel completes.
+ *  - out_host: caller-owned host memory of 8*streams*iterations bytes in
+ *    the same layout.  Values are produced in two device buffers that
+ *    alternate (generation into one while the other is copied to the host
+ *    on a separate copy stream, ordered by CUDA events).  Page-locked
+ *    memory is written directly by the copy engine; pageable memory goes
+ *    through the library's pinned staging slots.  Blocks until every value
+ *    is in out_host (the paper's blocking read).
+ * iterations == 0 is a no-op.  Errors: RNG_EINVAL (both or neither output,
+ * size overflow), RNG_ESTATE (not initialised), RNG_ECUDA. */
+int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev,
+                 uint64_t *out_host, rng_err **err);
+
+/* Host consumer ("out" block of Section 5).  Called on a library thread,
+ * in order, once per chunk of finished values: `values` holds `rows`
+ * consecutive iterations starting at absolute iteration `first_iteration`,
+ * each row covering streams first_stream .. first_stream+n_streams-1
+ * (relative to this generator), rows `row_pitch` values apart.  The
+ * memory is a pinned staging slot, valid only during the call.  A
+ * non-zero return stops the run with RNG_ESINK. */
+typedef int (*rng_sink_fn)(void *user, uint64_t first_iteration, uint64_t rows,
+                           uint64_t first_stream, uint64_t n_streams,
+                           uint64_t row_pitch, const uint64_t *values);
+
+/* Like rng_generate with host output, but hands each chunk to `sink`
+ * instead of a caller buffer (streams of any length, e.g. to a pipe).
+ * Blocks until the last chunk has been consumed. */
+int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink,
+                      void *user, rng_err **err);
+
+/* Generate-and-checksum mode: advances the streams through iterations
+ * p .. p+iterations-1 without storing the values and writes, for each
+ * iteration, the XOR (row_xor_dev[it-p]) and the wrapping sum modulo 2^64
+ * (row_sum_dev[it-p]) of that iteration's values over all streams.  Both
+ * arrays are caller-owned device memory of `iterations` uint64 words; the
+ * call clears them first.  Ordered on the compute stream. */
+int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev,
+                          uint64_t *row_sum_dev, rng_err **err);
+
+/* Current position p (next iteration to be emitted) and stream count. */
+int rng_position(const rng_gen *g, uint64_t *position);
+int rng_streams(const rng_gen *g, uint64_t *streams);
+/* Copies the current states (s_p of each stream) to host memory. Blocks. */
+int rng_get_state(rng_gen *g, uint64_t *host_states, rng_err **err);
+/* Waits for all work the generator has queued. */
+int rng_sync(rng_gen *g, rng_err **err);
+/* The compute stream (cudaStream_t) the generator launches on. */
+void *rng_compute_stream(rng_gen *g);
+/* Launch configuration chosen for `streams`: values per thread, threads
+ * per block and blocks of the grid. */
+int rng_launch_config(const rng_gen *g, uint32_t *values_per_thread,
+                      uint32_t *block_threads, uint32_t *grid_blocks);
+
+/* Releases the device state, buffers, streams and events.  NULL-safe. */
+void rng_destroy(rng_gen *g);
+
+/* ------------------------------------------------------------------ */
+/* Profiler (Section 3.3 and the profiling summary of Section 4.1)     */
+/* ------------------------------------------------------------------ */
+typedef struct rng_prof rng_prof;
+
+/* Sort flags for summaries: by name or by time/duration, optionally
+ * descending. */
+enum {
+    RNG_PROF_SORT_NAME = 0,
+    RNG_PROF_SORT_TIME = 1,
+    RNG_PROF_SORT_DESC = 0x10
+};
+
+/* A stand-alone profiler fed with explicit event intervals (seconds).
+ * Host-only: usable without a GPU. */
+rng_prof *rng_prof_new(void);
+int rng_prof_add(rng_prof *p, const char *queue, const char *name,
+                 double start_s, double end_s);
+/* Wall time of the profiled region ("Total elapsed time"). */
+int rng_prof_set_elapsed(rng_prof *p, double elapsed_s);
+/* Aggregates per event name, pairwise overlaps of events on different
+ * queues (summed per ordered pair: event that started later, event
+ * already running), effective time = total - overlaps, device share =
+ * effective / elapsed. */
+int rng_prof_calc(rng_prof *p, rng_err **err);
+size_t rng_prof_num_aggregates(const rng_prof *p);
+int rng_prof_aggregate(const rng_prof *p, size_t index, const char **name,
+                       double *abs_s, double *rel_pct);
+size_t rng_prof_num_overlaps(const rng_prof *p);
+int rng_prof_overlap(const rng_prof *p, size_t index, const char **name1,
+                     const char **name2, double *duration_s);
+double rng_prof_total(const rng_prof *p);
+double rng_prof_effective(const rng_prof *p);
+double rng_prof_elapsed(const rng_prof *p);
+/* Text summary in the layout of the paper's figure (aggregate table,
+ * overlap table, effective/elapsed/device/host lines).  Owned by p. */
+const char *rng_prof_summary(rng_prof *p, int agg_sort, int ovl_sort);
+/* Table of all events: one line "queue<TAB>start<TAB>end<TAB>name" per
+ * event, times in nanoseconds from the first event, ordered by start. */
+int rng_prof_export(rng_prof *p, const char *path, rng_err **err);
+void rng_prof_destroy(rng_prof *p);
+
+/* The generator's own profiler: every kernel ("INIT_KERNEL",
+ * "RNG_KERNEL", "CHECKSUM_KERNEL") on queue "Main" and every device-to-host
+ * copy ("READ_BUFFER") on queue "Comms" since creation or the last reset,
+ * timed with CUDA events recorded on the stream the work ran on.  Waits for
+ * that work.  Owned by g.  NULL on error. */
+rng_prof *rng_profiler(rng_gen *g, rng_err **err);
+const char *rng_profile_summary(rng_gen *g, int agg_sort, int ovl_sort, rng_err **err);
+int rng_profile_export(rng_gen *g, const char *path, rng_err **err);
+/* Drops recorded events and restarts the wall clock. */
+int rng_profile_reset(rng_gen *g, rng_err **err);
+/* Count and summed device time (seconds) of the recorded events with this
+ * name.  Waits for them. */
+int rng_profile_stat(rng_gen *g, const char *name, uint64_t *count,
+                     double *total_s, rng_err **err);
+
+/* ------------------------------------------------------------------ */
+/* Batched form: many independent generators in one graph launch       */
+/* ------------------------------------------------------------------ */
+typedef struct rng_batch rng_batch;
+
+typedef struct rng_batch_opts {
+    uint32_t struct_size;
+    uint32_t values_per_thread;  /* 0 = autotune over {1,2,4,8,16,32} */
+    uint32_t block_threads;      /* 0 = 256 */
+    uint32_t tune_reps;          /* timed replays per candidate (default 3) */
+    void *stream;                /* cudaStream_t; NULL = own stream */
+    int32_t device;              /* -1 = current */
+} rng_batch_opts;
+
+void rng_batch_opts_default(rng_batch_opts *opts);
+
+/* `count` independent instances; instance k has streams[k] streams
+ * (1 .. 2^32), iterations[k] iterations (>= 1), run seed seeds[k] and
+ * writes its iterations 0 .. iterations[k]-1 to outs[k], caller-owned
+ * device memory of 8*streams[k]*iterations[k] bytes, in its own
+ * iteration-major layout.  Builds the work table, picks the launch shape
+ * (autotuned unless fixed in opts) and captures one persistent launch in a
+ * CUDA graph.  Output arrays are written during tuning. */
+int rng_batch_create(uint32_t count, const uint64_t *streams,
+                     const uint64_t *iterations, const uint64_t *seeds,
+                     uint64_t *const *outs, const rng_batch_opts *opts,
+                     rng_batch **out, rng_err **err);
+/* Replays the captured graph on the batch's stream; asynchronous. */
+int rng_batch_run(rng_batch *b, rng_err **err);
+int rng_batch_sync(rng_batch *b, rng_err **err);
+/* Chosen shape and the tuned time of one replay (ms; 0 if not tuned). */
+int rng_batch_config(const rng_batch *b, uint32_t *values_per_thread,
+                     uint32_t *block_threads, uint32_t *grid_blocks,
+                     uint64_t *work_units, double *tuned_ms);
+void *rng_batch_stream(rng_batch *b);
+void rng_batch_destroy(rng_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRNG_GB300_RNG_H */

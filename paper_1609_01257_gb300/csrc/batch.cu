@@ -1,0 +1,248 @@
+// Batched form: many independent generator instances (each its own stream
+// count, iteration count and seed, each starting at iteration 0) produced by
+// one persistent kernel launch captured in a CUDA graph.
+//
+// Work is cut into units of one tile (256 threads x values-per-thread
+// streams) of one instance, with all of that instance's iterations.  Units are
+// ordered by decreasing output bytes and handed out through a device counter,
+// so the longest units start first and blocks that finish early take the
+// short ones.  The autotuner times the graph for each values-per-thread
+// candidate and keeps the fastest; every candidate writes the same bytes.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "prng_math.cuh"
+
+struct rng_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<rngi::BatchInstance> inst;
+  rngi::BatchInstance *d_inst = nullptr;
+  rngi::BatchUnit *d_units = nullptr;
+  size_t units_cap = 0;
+  uint32_t *d_counter = nullptr;
+  uint32_t n_units = 0;
+  uint32_t vpt = 0, block = 256, grid = 0;
+  double tuned_ms = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+const uint32_t kBlock = 256;
+
+void drop_graph(rng_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Builds the unit table for `vpt`, uploads it and captures the graph.
+int prepare(rng_batch *b, uint32_t vpt, rng_err **err) {
+  const uint64_t tile = uint64_t(kBlock) * vpt;
+  std::vector<rngi::BatchUnit> units;
+  for (uint32_t k = 0; k < b->inst.size(); ++k)
+    for (uint64_t s = 0; s < b->inst[k].streams; s += tile) {
+      const uint64_t c = std::min<uint64_t>(tile, b->inst[k].streams - s);
+      units.push_back({k, static_cast<uint32_t>(c), s});
+    }
+  if (units.size() > 0xffffffffull) return rngi::fail(err, RNG_EINVAL, "rng_batch: too many work units");
+  std::stable_sort(units.begin(), units.end(), [&](const rngi::BatchUnit &x, const rngi::BatchUnit &y) {
+    return uint64_t(x.count) * b->inst[x.inst].rows > uint64_t(y.count) * b->inst[y.inst].rows;
+  });
+  if (units.size() > b->units_cap) {
+    cudaFree(b->d_units);
+    b->d_units = nullptr;
+    int rc = rngi::cuda_fail(err, cudaMalloc(&b->d_units, units.size() * sizeof(rngi::BatchUnit)),
+                             "cudaMalloc(batch units)");
+    if (rc) return rc;
+    b->units_cap = units.size();
+  }
+  int rc = rngi::cuda_fail(err,
+                           cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(rngi::BatchUnit),
+                                           cudaMemcpyHostToDevice, b->stream),
+                           "cudaMemcpy(batch units)");
+  if (rc) return rc;
+  rc = rngi::cuda_fail(err, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+  if (rc) return rc;
+  b->n_units = static_cast<uint32_t>(units.size());
+  b->vpt = vpt;
+  b->block = kBlock;
+  const int per_sm = rngi::batch_blocks_per_sm(vpt, kBlock);
+  const uint64_t resident = uint64_t(rngi::device_sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
+  b->grid = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(resident, b->n_units)));
+
+  drop_graph(b);
+  cudaError_t st = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (st == cudaSuccess) {
+    cudaError_t s1 = cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), b->stream);
+    cudaError_t s2 = rngi::launch_batch(b->d_inst, b->d_units, b->n_units, b->d_counter, vpt, kBlock,
+                                        b->grid, b->stream);
+    st = cudaStreamEndCapture(b->stream, &b->graph);
+    if (st == cudaSuccess) st = s1 != cudaSuccess ? s1 : s2;
+  }
+  if (st == cudaSuccess) st = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  return rngi::cuda_fail(err, st, "batch graph capture");
+}
+
+int replay(rng_batch *b, rng_err **err) {
+  cudaError_t st = cudaGraphLaunch(b->exec, b->stream);
+  if (st == cudaSuccess) rngi::count_launch();
+  return rngi::cuda_fail(err, st, "cudaGraphLaunch");
+}
+
+}  // namespace
+
+extern "C" {
+
+void rng_batch_opts_default(rng_batch_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(rng_batch_opts);
+  o->values_per_thread = 0;
+  o->block_threads = 0;
+  o->tune_reps = 3;
+  o->stream = nullptr;
+  o->device = -1;
+}
+
+int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *iterations,
+                     const uint64_t *seeds, uint64_t *const *outs, const rng_batch_opts *opts,
+                     rng_batch **out, rng_err **err) {
+  if (!out) return rngi::fail(err, RNG_EINVAL, "rng_batch_create: NULL output pointer");
+  *out = nullptr;
+  if (count == 0 || !streams || !iterations || !seeds || !outs)
+    return rngi::fail(err, RNG_EINVAL, "rng_batch_create: empty batch or NULL array");
+  rng_batch_opts o;
+  rng_batch_opts_default(&o);
+  if (opts) {
+    if (opts->struct_size != sizeof(rng_batch_opts))
+      return rngi::fail(err, RNG_EINVAL, "rng_batch_create: opts.struct_size mismatch");
+    o = *opts;
+  }
+  const uint32_t v = o.values_per_thread;
+  if (v && (v > 32 || (v & (v - 1))))
+    return rngi::fail(err, RNG_EINVAL, "rng_batch_create: values_per_thread must be 0 or 1..32 (power of two)");
+  if (o.block_threads && o.block_threads != kBlock)
+    return rngi::fail(err, RNG_EINVAL, "rng_batch_create: block_threads must be 0 or 256");
+  for (uint32_t k = 0; k < count; ++k) {
+    if (streams[k] == 0 || streams[k] > (uint64_t(1) << 32) || iterations[k] == 0 || !outs[k])
+      return rngi::fail(err, RNG_EINVAL, "rng_batch_create: instance %u has an invalid size or output", k);
+    if (iterations[k] > (~uint64_t(0) / 8) / streams[k])
+      return rngi::fail(err, RNG_EINVAL, "rng_batch_create: instance %u output size overflows", k);
+    if (reinterpret_cast<uintptr_t>(outs[k]) % 8)
+      return rngi::fail(err, RNG_EINVAL, "rng_batch_create: instance %u output not 8-byte aligned", k);
+  }
+  int dev = o.device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return rngi::fail(err, RNG_ECUDA, "cudaGetDevice failed");
+  cudaError_t st = cudaSetDevice(dev);
+  if (st != cudaSuccess) return rngi::cuda_fail(err, st, "cudaSetDevice");
+
+  rng_batch *b = new (std::nothrow) rng_batch();
+  if (!b) return rngi::fail(err, RNG_ENOMEM, "rng_batch_create: host allocation failed");
+  rngi::live_inc();
+  b->device = dev;
+  for (uint32_t k = 0; k < count; ++k) {
+    rngi::BatchInstance in;
+    in.out = outs[k];
+    in.streams = streams[k];
+    in.rows = iterations[k];
+    in.key = prng::seed_key(seeds[k]);
+    in.vec = (streams[k] % 2 == 0) && (reinterpret_cast<uintptr_t>(outs[k]) % 16 == 0);
+    b->inst.push_back(in);
+  }
+  int rc = RNG_OK;
+  if (o.stream) {
+    b->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    b->own_stream = rc == RNG_OK;
+  }
+  if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&b->d_inst, count * sizeof(rngi::BatchInstance)), "cudaMalloc(batch)");
+  if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&b->d_counter, sizeof(uint32_t)), "cudaMalloc(batch counter)");
+  if (!rc)
+    rc = rngi::cuda_fail(err, cudaMemcpyAsync(b->d_inst, b->inst.data(), count * sizeof(rngi::BatchInstance),
+                                              cudaMemcpyHostToDevice, b->stream),
+                         "cudaMemcpy(batch)");
+  if (!rc && v) rc = prepare(b, v, err);
+  if (!rc && !v) {
+    // Autotune: time each candidate's graph and keep the fastest.
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = rngi::cuda_fail(err, cudaEventCreate(&e0), "cudaEventCreate");
+    if (!rc) rc = rngi::cuda_fail(err, cudaEventCreate(&e1), "cudaEventCreate");
+    const uint32_t reps = o.tune_reps ? o.tune_reps : 3;
+    uint32_t best_v = 0;
+    double best_ms = 0.0;
+    for (uint32_t cand = 1; cand <= 32 && !rc; cand *= 2) {
+      rc = prepare(b, cand, err);
+      if (!rc) rc = replay(b, err);  // warm-up
+      if (!rc) rc = rngi::cuda_fail(err, cudaEventRecord(e0, b->stream), "cudaEventRecord");
+      for (uint32_t r = 0; r < reps && !rc; ++r) rc = replay(b, err);
+      if (!rc) rc = rngi::cuda_fail(err, cudaEventRecord(e1, b->stream), "cudaEventRecord");
+      if (!rc) rc = rngi::cuda_fail(err, cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float ms = 0.f;
+      if (!rc) rc = rngi::cuda_fail(err, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      if (!rc && (best_v == 0 || ms / reps < best_ms)) {
+        best_v = cand;
+        best_ms = ms / reps;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!rc) rc = prepare(b, best_v, err);
+    if (!rc) b->tuned_ms = best_ms;
+  }
+  if (rc) {
+    rng_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return RNG_OK;
+}
+
+int rng_batch_run(rng_batch *b, rng_err **err) {
+  if (!b) return rngi::fail(err, RNG_EINVAL, "rng_batch_run: NULL batch");
+  if (cudaSetDevice(b->device) != cudaSuccess) return rngi::fail(err, RNG_ECUDA, "rng_batch_run: cudaSetDevice");
+  return replay(b, err);
+}
+
+int rng_batch_sync(rng_batch *b, rng_err **err) {
+  if (!b) return rngi::fail(err, RNG_EINVAL, "rng_batch_sync: NULL batch");
+  return rngi::cuda_fail(err, cudaStreamSynchronize(b->stream), "rng_batch_sync");
+}
+
+int rng_batch_config(const rng_batch *b, uint32_t *vpt, uint32_t *block, uint32_t *grid, uint64_t *units,
+                     double *tuned_ms) {
+  if (!b) return RNG_EINVAL;
+  if (vpt) *vpt = b->vpt;
+  if (block) *block = b->block;
+  if (grid) *grid = b->grid;
+  if (units) *units = b->n_units;
+  if (tuned_ms) *tuned_ms = b->tuned_ms;
+  return RNG_OK;
+}
+
+void *rng_batch_stream(rng_batch *b) { return b ? static_cast<void *>(b->stream) : nullptr; }
+
+void rng_batch_destroy(rng_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  cudaFree(b->d_inst);
+  cudaFree(b->d_units);
+  cudaFree(b->d_counter);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  rngi::live_dec();
+}
+
+}  // extern "C"

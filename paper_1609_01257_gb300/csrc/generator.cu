@@ -1,0 +1,694 @@
+// Generator object: device state, launch shape, the device-side double
+// buffer with its copy stream (Section 5 of the cf4ocl paper: generation into
+// one buffer while the other is read to the host), the host consumer, and the
+// CUDA-event profiler glue.
+//
+// The paper orders its two threads with two semaphores: the read of batch k
+// must finish before the kernel that overwrites its buffer starts, and the
+// kernel producing batch k must finish before its read starts.  Here the
+// same two orders are CUDA events between the compute stream and the copy
+// stream (`copied[b]` and `produced[b]`), so neither host thread blocks on
+// the device between launches.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+#include "prng_math.cuh"
+
+namespace rngi {
+void prof_clear(rng_prof *p);
+void prof_add(rng_prof *p, const char *queue, const char *name, double s, double e);
+}  // namespace rngi
+
+namespace {
+
+constexpr const char *kQueueMain = "Main";
+constexpr const char *kQueueComms = "Comms";
+constexpr size_t kMaxOps = size_t(1) << 20;
+
+struct OpRec {
+  const char *name;
+  const char *queue;
+  size_t ev0, ev1;
+};
+
+}  // namespace
+
+struct rng_gen {
+  uint64_t n = 0, seed = 0, g0 = 0, pos = 0;
+  uint32_t key = 0;
+  int device = 0;
+  bool initialized = false;   // rng_init called and no failed run since
+  bool materialized = false;  // state array holds s_pos (else: hash of the ids)
+  rng_opts opts{};
+  rngi::LaunchShape shape{};
+  rngi::LaunchShape chunk_shape{};  // shape of the last streamed chunk width
+  uint64_t chunk_span = 0;
+  uint64_t *d_state = nullptr;
+  cudaStream_t compute = nullptr, copy = nullptr;
+  bool own_compute = false;
+  uint64_t *d_buf[2] = {nullptr, nullptr};
+  size_t buf_bytes = 0;
+  std::vector<void *> h_slots;
+  std::vector<cudaEvent_t> slot_ready;
+  cudaEvent_t produced[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+  // profiling
+  std::vector<cudaEvent_t> evpool;
+  size_t ev_used = 0;
+  std::vector<OpRec> ops;
+  cudaEvent_t origin = nullptr;
+  std::chrono::steady_clock::time_point wall0;
+  rng_prof *prof = nullptr;
+  std::string summary;
+};
+
+namespace {
+
+bool is_pow2_upto(uint32_t v, uint32_t cap) { return v && v <= cap && (v & (v - 1)) == 0; }
+
+cudaError_t next_event(rng_gen *g, size_t *idx) {
+  if (g->ev_used == g->evpool.size()) {
+    cudaEvent_t e;
+    cudaError_t st = cudaEventCreate(&e);
+    if (st != cudaSuccess) return st;
+    g->evpool.push_back(e);
+  }
+  *idx = g->ev_used++;
+  return cudaSuccess;
+}
+
+// Records the start event of an op on `s`; returns the op slot or -1 when
+// profiling is off or the op log is full.
+long op_begin(rng_gen *g, const char *name, const char *queue, cudaStream_t s) {
+  if (!g->opts.profiling || g->ops.size() >= kMaxOps) return -1;
+  size_t e0;
+  if (next_event(g, &e0) != cudaSuccess) return -1;
+  if (cudaEventRecord(g->evpool[e0], s) != cudaSuccess) return -1;
+  g->ops.push_back({name, queue, e0, e0});
+  return static_cast<long>(g->ops.size() - 1);
+}
+
+void op_end(rng_gen *g, long op, cudaStream_t s) {
+  if (op < 0) return;
+  size_t e1;
+  if (next_event(g, &e1) != cudaSuccess || cudaEventRecord(g->evpool[e1], s) != cudaSuccess) {
+    g->ops.pop_back();
+    return;
+  }
+  g->ops[op].ev1 = e1;
+}
+
+int profile_restart(rng_gen *g, rng_err **err) {
+  g->ops.clear();
+  g->ev_used = 0;
+  g->wall0 = std::chrono::steady_clock::now();
+  if (!g->origin) {
+    int rc = rngi::cuda_fail(err, cudaEventCreate(&g->origin), "cudaEventCreate");
+    if (rc) return rc;
+  }
+  return rngi::cuda_fail(err, cudaEventRecord(g->origin, g->compute), "cudaEventRecord");
+}
+
+int ensure_buffers(rng_gen *g, bool staged, rng_err **err) {
+  if (!g->d_buf[0]) {
+    for (int b = 0; b < 2; ++b) {
+      int rc = rngi::cuda_fail(err, cudaMalloc(&g->d_buf[b], g->buf_bytes), "cudaMalloc(device buffer)");
+      if (rc) return rc;
+      rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&g->produced[b], cudaEventDisableTiming),
+                           "cudaEventCreate");
+      if (rc) return rc;
+      rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&g->copied[b], cudaEventDisableTiming),
+                           "cudaEventCreate");
+      if (rc) return rc;
+    }
+  }
+  if (staged && g->h_slots.empty()) {
+    const uint32_t n = g->opts.host_slots < 2 ? 2 : g->opts.host_slots;
+    for (uint32_t i = 0; i < n; ++i) {
+      void *p = nullptr;
+      int rc = rngi::cuda_fail(err, cudaHostAlloc(&p, g->buf_bytes, cudaHostAllocDefault),
+                               "cudaHostAlloc(staging slot)");
+      if (rc) return rc;
+      g->h_slots.push_back(p);
+      cudaEvent_t e;
+      rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+      if (rc) return rc;
+      g->slot_ready.push_back(e);
+    }
+  }
+  return RNG_OK;
+}
+
+struct Chunk {
+  uint64_t r0, rows;     // iterations relative to the call's first one
+  uint64_t s0, span;     // stream range
+};
+
+// Splits `T` iterations of `n` streams into chunks that fit one device buffer:
+// whole rows when a row fits (as many rows as fit), else one row split into
+// column slabs.
+std::vector<Chunk> plan_chunks(uint64_t n, uint64_t T, size_t buf_bytes) {
+  std::vector<Chunk> v;
+  const uint64_t cap_vals = buf_bytes / 8;
+  if (n <= cap_vals) {
+    const uint64_t R = cap_vals / n;
+    for (uint64_t r = 0; r < T; r += R) v.push_back({r, (T - r) < R ? (T - r) : R, 0, n});
+  } else {
+    const uint64_t C = cap_vals & ~uint64_t(1);
+    for (uint64_t r = 0; r < T; ++r)
+      for (uint64_t s = 0; s < n; s += C) v.push_back({r, 1, s, (n - s) < C ? (n - s) : C});
+  }
+  return v;
+}
+
+int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_err **err) {
+  rngi::RowsLaunch a{};
+  a.state = g->d_state;
+  a.out = dst;
+  a.pitch = c.span;
+  a.s_begin = c.s0;
+  a.s_end = c.s0 + c.span;
+  a.id_base = g->g0;
+  a.rows = c.rows;
+  a.key = g->key;
+  a.from_hash = from_hash;
+  a.write_state = 1;
+  if (c.span != g->chunk_span) {
+    g->chunk_shape = rngi::rows_shape(c.span, g->opts.values_per_thread, g->opts.block_threads, g->device);
+    g->chunk_span = c.span;
+  }
+  const rngi::LaunchShape sh = g->chunk_shape;
+  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
+  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute);
+  op_end(g, op, g->compute);
+  return rngi::cuda_fail(err, st, "rows kernel launch");
+}
+
+// Host consumer thread for staged output (pageable destination or sink).
+struct Consumer {
+  struct Job {
+    Chunk c;
+    size_t slot;
+    bool stop;
+  };
+  rng_gen *g;
+  uint64_t *out_host;
+  uint64_t first_iteration;
+  rng_sink_fn sink;
+  void *user;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Job> jobs;
+  std::vector<bool> slot_free;
+  int status = RNG_OK;
+  std::string msg;
+  std::thread th;
+
+  void run() {
+    for (;;) {
+      Job j;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return !jobs.empty(); });
+        j = jobs.front();
+        jobs.pop_front();
+      }
+      if (j.stop) return;
+      int rc = RNG_OK;
+      std::string m;
+      {
+        bool skip;
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          skip = status != RNG_OK;
+        }
+        if (!skip) {
+          cudaError_t st = cudaEventSynchronize(g->slot_ready[j.slot]);
+          const uint64_t *vals = static_cast<const uint64_t *>(g->h_slots[j.slot]);
+          if (st != cudaSuccess) {
+            rc = RNG_ECUDA;
+            m = std::string("cudaEventSynchronize: ") + cudaGetErrorString(st);
+          } else if (out_host) {
+            memcpy(out_host + j.c.r0 * g->n + j.c.s0, vals, j.c.rows * j.c.span * 8);
+          } else {
+            int urc = sink(user, first_iteration + j.c.r0, j.c.rows, j.c.s0, j.c.span, j.c.span, vals);
+            if (urc) {
+              rc = RNG_ESINK;
+              m = "host consumer returned " + std::to_string(urc);
+            }
+          }
+        }
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        if (rc != RNG_OK && status == RNG_OK) {
+          status = rc;
+          msg = m;
+        }
+        slot_free[j.slot] = true;
+      }
+      cv.notify_all();
+    }
+  }
+};
+
+int staged_or_direct(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn sink, void *user,
+                     rng_err **err) {
+  bool pinned = false;
+  if (out_host) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost)
+      pinned = true;
+    cudaGetLastError();
+  }
+  const bool staged = !pinned;
+  int rc = ensure_buffers(g, staged, err);
+  if (rc) return rc;
+  const std::vector<Chunk> chunks = plan_chunks(g->n, T, g->buf_bytes);
+  const bool hash_first_rows = !g->materialized;
+  const uint64_t first_it = g->pos;
+  g->initialized = false;  // re-armed only if the whole run succeeds
+
+  Consumer cons;
+  cons.g = g;
+  cons.out_host = out_host;
+  cons.first_iteration = first_it;
+  cons.sink = sink;
+  cons.user = user;
+  if (staged) {
+    cons.slot_free.assign(g->h_slots.size(), true);
+    cons.th = std::thread([&cons] { cons.run(); });
+  }
+  const auto wait_limit = std::chrono::milliseconds(g->opts.host_wait_ms ? g->opts.host_wait_ms : 600000);
+
+  int status = RNG_OK;
+  std::string status_msg;
+  for (size_t c = 0; c < chunks.size() && status == RNG_OK; ++c) {
+    const Chunk &ck = chunks[c];
+    const int b = static_cast<int>(c & 1);
+    size_t slot = 0;
+    if (staged) {
+      slot = c % g->h_slots.size();
+      std::unique_lock<std::mutex> lk(cons.mu);
+      const bool ok = cons.cv.wait_for(lk, wait_limit,
+                                       [&] { return cons.slot_free[slot] || cons.status != RNG_OK; });
+      if (cons.status != RNG_OK) break;
+      if (!ok) {
+        status = RNG_ETIMEOUT;
+        status_msg = "no staging slot freed by the host consumer within the wait limit";
+        cons.status = RNG_ETIMEOUT;
+        break;
+      }
+      cons.slot_free[slot] = false;
+    }
+    cudaError_t st = cudaSuccess;
+    if (c >= 2) st = cudaStreamWaitEvent(g->compute, g->copied[b], 0);
+    if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "cudaStreamWaitEvent"); break; }
+    status = launch_chunk(g, ck, hash_first_rows && ck.r0 == 0, g->d_buf[b], err);
+    if (status) break;
+    st = cudaEventRecord(g->produced[b], g->compute);
+    if (st == cudaSuccess) st = cudaStreamWaitEvent(g->copy, g->produced[b], 0);
+    if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "event ordering"); break; }
+    void *dst = staged ? g->h_slots[slot] : static_cast<void *>(out_host + ck.r0 * g->n + ck.s0);
+    long op = op_begin(g, "READ_BUFFER", kQueueComms, g->copy);
+    st = cudaMemcpyAsync(dst, g->d_buf[b], ck.rows * ck.span * 8, cudaMemcpyDeviceToHost, g->copy);
+    op_end(g, op, g->copy);
+    if (st == cudaSuccess) st = cudaEventRecord(g->copied[b], g->copy);
+    if (st == cudaSuccess && staged) st = cudaEventRecord(g->slot_ready[slot], g->copy);
+    if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "device-to-host copy"); break; }
+    if (staged) {
+      {
+        std::lock_guard<std::mutex> lk(cons.mu);
+        cons.jobs.push_back({ck, slot, false});
+      }
+      cons.cv.notify_all();
+    }
+  }
+  if (staged) {
+    {
+      std::lock_guard<std::mutex> lk(cons.mu);
+      cons.jobs.push_back({Chunk{}, 0, true});
+    }
+    cons.cv.notify_all();
+    cons.th.join();
+    if (status == RNG_OK && cons.status != RNG_OK) {
+      status = cons.status;
+      status_msg = cons.msg;
+    }
+  }
+  cudaError_t st = cudaStreamSynchronize(g->copy);
+  cudaError_t st2 = cudaStreamSynchronize(g->compute);
+  if (status == RNG_OK && st != cudaSuccess) status = rngi::cuda_fail(err, st, "cudaStreamSynchronize(copy)");
+  if (status == RNG_OK && st2 != cudaSuccess) status = rngi::cuda_fail(err, st2, "cudaStreamSynchronize(compute)");
+  if (status != RNG_OK) {
+    if (!status_msg.empty()) rngi::fail(err, status, "rng_generate: %s", status_msg.c_str());
+    return status;  // streams partly advanced: rng_init required again
+  }
+  g->materialized = true;
+  g->pos += T;
+  g->initialized = true;
+  return RNG_OK;
+}
+
+int check_gen(const rng_gen *g, rng_err **err, const char *fn) {
+  if (!g) return rngi::fail(err, RNG_EINVAL, "%s: NULL generator", fn);
+  if (cudaSetDevice(g->device) != cudaSuccess)
+    return rngi::fail(err, RNG_ECUDA, "%s: cannot select device %d", fn, g->device);
+  return RNG_OK;
+}
+
+int size_ok(uint64_t n, uint64_t T, rng_err **err) {
+  if (T > (~uint64_t(0) / 8) / n) return rngi::fail(err, RNG_EINVAL, "output size 8*%llu*%llu overflows",
+                                                    (unsigned long long)n, (unsigned long long)T);
+  return RNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rng_opts_default(rng_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(rng_opts);
+  o->values_per_thread = 0;
+  o->block_threads = 0;
+  o->fuse_init = 1;
+  o->stream_offset = 0;
+  o->device_buffer_bytes = size_t(32) << 20;
+  o->host_slots = 2;
+  o->profiling = 1;
+  o->compute_stream = nullptr;
+  o->device = -1;
+  o->store_policy = 0;
+  o->host_wait_ms = 0;
+}
+
+int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **out, rng_err **err) {
+  if (!out) return rngi::fail(err, RNG_EINVAL, "rng_create: NULL output pointer");
+  *out = nullptr;
+  if (streams == 0 || streams > (uint64_t(1) << 32))
+    return rngi::fail(err, RNG_EINVAL, "rng_create: streams must be in [1, 2^32], got %llu",
+                      (unsigned long long)streams);
+  rng_opts o;
+  rng_opts_default(&o);
+  if (opts) {
+    if (opts->struct_size != sizeof(rng_opts))
+      return rngi::fail(err, RNG_EINVAL, "rng_create: opts.struct_size %u != %zu", opts->struct_size,
+                        sizeof(rng_opts));
+    o = *opts;
+  }
+  if (o.values_per_thread && !is_pow2_upto(o.values_per_thread, 64))
+    return rngi::fail(err, RNG_EINVAL, "rng_create: values_per_thread must be 0 or a power of two <= 64");
+  if (o.block_threads && o.block_threads != 256)
+    return rngi::fail(err, RNG_EINVAL, "rng_create: block_threads must be 0 or 256");
+  if (o.device_buffer_bytes == 0) o.device_buffer_bytes = size_t(32) << 20;
+  if (o.device_buffer_bytes < 16 || o.device_buffer_bytes % 16)
+    return rngi::fail(err, RNG_EINVAL, "rng_create: device_buffer_bytes must be a positive multiple of 16");
+  if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
+  if (o.stream_offset > (uint64_t(1) << 32) - streams)
+    return rngi::fail(err, RNG_EINVAL, "rng_create: stream_offset + streams must not exceed 2^32");
+
+  int dev = o.device;
+  if (dev < 0) {
+    cudaError_t st = cudaGetDevice(&dev);
+    if (st != cudaSuccess) return rngi::cuda_fail(err, st, "cudaGetDevice");
+  }
+  cudaError_t st = cudaSetDevice(dev);
+  if (st != cudaSuccess) return rngi::cuda_fail(err, st, "cudaSetDevice");
+
+  rng_gen *g = new (std::nothrow) rng_gen();
+  if (!g) return rngi::fail(err, RNG_ENOMEM, "rng_create: host allocation failed");
+  g->n = streams;
+  g->seed = seed;
+  g->g0 = o.stream_offset;
+  g->key = prng::seed_key(seed);
+  g->device = dev;
+  g->opts = o;
+  g->buf_bytes = o.device_buffer_bytes;
+  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev);
+  rngi::live_inc();
+  int rc = RNG_OK;
+  if (o.compute_stream) {
+    g->compute = static_cast<cudaStream_t>(o.compute_stream);
+  } else {
+    rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&g->compute, cudaStreamNonBlocking), "cudaStreamCreate");
+    g->own_compute = rc == RNG_OK;
+  }
+  if (!rc) rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&g->copy, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&g->d_state, streams * 8), "cudaMalloc(state)");
+  if (!rc) rc = profile_restart(g, err);
+  if (!rc) g->prof = rng_prof_new();
+  if (!rc && !g->prof) rc = rngi::fail(err, RNG_ENOMEM, "rng_create: profiler allocation failed");
+  if (rc) {
+    rng_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return RNG_OK;
+}
+
+void rng_destroy(rng_gen *g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->compute) cudaStreamSynchronize(g->compute);
+  if (g->copy) cudaStreamSynchronize(g->copy);
+  cudaFree(g->d_state);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(g->d_buf[b]);
+    if (g->produced[b]) cudaEventDestroy(g->produced[b]);
+    if (g->copied[b]) cudaEventDestroy(g->copied[b]);
+  }
+  for (void *p : g->h_slots) cudaFreeHost(p);
+  for (cudaEvent_t e : g->slot_ready) cudaEventDestroy(e);
+  for (cudaEvent_t e : g->evpool) cudaEventDestroy(e);
+  if (g->origin) cudaEventDestroy(g->origin);
+  if (g->copy) cudaStreamDestroy(g->copy);
+  if (g->own_compute && g->compute) cudaStreamDestroy(g->compute);
+  rng_prof_destroy(g->prof);
+  delete g;
+  rngi::live_dec();
+}
+
+int rng_init(rng_gen *g, rng_err **err) {
+  int rc = check_gen(g, err, "rng_init");
+  if (rc) return rc;
+  g->pos = 0;
+  g->materialized = false;
+  if (!g->opts.fuse_init) {
+    long op = op_begin(g, "INIT_KERNEL", kQueueMain, g->compute);
+    cudaError_t st = rngi::launch_init(g->d_state, g->n, g->g0, g->key, g->compute);
+    op_end(g, op, g->compute);
+    rc = rngi::cuda_fail(err, st, "init kernel launch");
+    if (rc) return rc;
+    g->materialized = true;
+  }
+  g->initialized = true;
+  return RNG_OK;
+}
+
+int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *out_host, rng_err **err) {
+  int rc = check_gen(g, err, "rng_generate");
+  if (rc) return rc;
+  if ((out_dev == nullptr) == (out_host == nullptr))
+    return rngi::fail(err, RNG_EINVAL, "rng_generate: exactly one of out_dev and out_host must be set");
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_generate: generator not initialised (call rng_init)");
+  if (iterations == 0) return RNG_OK;
+  rc = size_ok(g->n, iterations, err);
+  if (rc) return rc;
+  if (out_host) return staged_or_direct(g, iterations, out_host, nullptr, nullptr, err);
+  if (reinterpret_cast<uintptr_t>(out_dev) % 8)
+    return rngi::fail(err, RNG_EINVAL, "rng_generate: out_dev must be 8-byte aligned");
+  rngi::RowsLaunch a{};
+  a.state = g->d_state;
+  a.out = out_dev;
+  a.pitch = g->n;
+  a.s_begin = 0;
+  a.s_end = g->n;
+  a.id_base = g->g0;
+  a.rows = iterations;
+  a.key = g->key;
+  a.from_hash = !g->materialized;
+  a.write_state = 1;
+  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
+  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
+  op_end(g, op, g->compute);
+  rc = rngi::cuda_fail(err, st, "rows kernel launch");
+  if (rc) return rc;
+  g->materialized = true;
+  g->pos += iterations;
+  return RNG_OK;
+}
+
+int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink, void *user, rng_err **err) {
+  int rc = check_gen(g, err, "rng_generate_sink");
+  if (rc) return rc;
+  if (!sink) return rngi::fail(err, RNG_EINVAL, "rng_generate_sink: NULL sink");
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_generate_sink: generator not initialised (call rng_init)");
+  if (iterations == 0) return RNG_OK;
+  rc = size_ok(g->n, iterations, err);
+  if (rc) return rc;
+  return staged_or_direct(g, iterations, nullptr, sink, user, err);
+}
+
+int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev, uint64_t *row_sum_dev,
+                          rng_err **err) {
+  int rc = check_gen(g, err, "rng_generate_checksum");
+  if (rc) return rc;
+  if (!row_xor_dev || !row_sum_dev) return rngi::fail(err, RNG_EINVAL, "rng_generate_checksum: NULL output");
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_generate_checksum: generator not initialised");
+  if (iterations == 0) return RNG_OK;
+  rc = size_ok(g->n, iterations, err);
+  if (rc) return rc;
+  cudaError_t st = cudaMemsetAsync(row_xor_dev, 0, iterations * 8, g->compute);
+  if (st == cudaSuccess) st = cudaMemsetAsync(row_sum_dev, 0, iterations * 8, g->compute);
+  rc = rngi::cuda_fail(err, st, "cudaMemsetAsync(checksums)");
+  if (rc) return rc;
+  rngi::RowsLaunch a{};
+  a.state = g->d_state;
+  a.out = nullptr;
+  a.pitch = 0;
+  a.s_begin = 0;
+  a.s_end = g->n;
+  a.id_base = g->g0;
+  a.rows = iterations;
+  a.key = g->key;
+  a.from_hash = !g->materialized;
+  a.write_state = 1;
+  long op = op_begin(g, "CHECKSUM_KERNEL", kQueueMain, g->compute);
+  st = rngi::launch_checksum(a, g->shape, row_xor_dev, row_sum_dev, g->compute);
+  op_end(g, op, g->compute);
+  rc = rngi::cuda_fail(err, st, "checksum kernel launch");
+  if (rc) return rc;
+  g->materialized = true;
+  g->pos += iterations;
+  return RNG_OK;
+}
+
+int rng_position(const rng_gen *g, uint64_t *position) {
+  if (!g || !position) return RNG_EINVAL;
+  *position = g->pos;
+  return RNG_OK;
+}
+
+int rng_streams(const rng_gen *g, uint64_t *streams) {
+  if (!g || !streams) return RNG_EINVAL;
+  *streams = g->n;
+  return RNG_OK;
+}
+
+int rng_get_state(rng_gen *g, uint64_t *host_states, rng_err **err) {
+  int rc = check_gen(g, err, "rng_get_state");
+  if (rc) return rc;
+  if (!host_states) return rngi::fail(err, RNG_EINVAL, "rng_get_state: NULL output");
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_get_state: generator not initialised");
+  if (!g->materialized) {
+    rc = rngi::cuda_fail(err, rngi::launch_init(g->d_state, g->n, g->g0, g->key, g->compute), "init kernel launch");
+    if (rc) return rc;
+    g->materialized = true;
+  }
+  cudaError_t st = cudaMemcpyAsync(host_states, g->d_state, g->n * 8, cudaMemcpyDeviceToHost, g->compute);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(g->compute);
+  return rngi::cuda_fail(err, st, "rng_get_state copy");
+}
+
+int rng_sync(rng_gen *g, rng_err **err) {
+  int rc = check_gen(g, err, "rng_sync");
+  if (rc) return rc;
+  cudaError_t st = cudaStreamSynchronize(g->compute);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(g->copy);
+  return rngi::cuda_fail(err, st, "rng_sync");
+}
+
+void *rng_compute_stream(rng_gen *g) { return g ? static_cast<void *>(g->compute) : nullptr; }
+
+int rng_launch_config(const rng_gen *g, uint32_t *vpt, uint32_t *block, uint32_t *grid) {
+  if (!g) return RNG_EINVAL;
+  if (vpt) *vpt = g->shape.vpt;
+  if (block) *block = g->shape.block;
+  if (grid) *grid = g->shape.grid;
+  return RNG_OK;
+}
+
+rng_prof *rng_profiler(rng_gen *g, rng_err **err) {
+  if (check_gen(g, err, "rng_profiler")) return nullptr;
+  cudaError_t st = cudaStreamSynchronize(g->compute);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(g->copy);
+  if (rngi::cuda_fail(err, st, "rng_profiler: synchronize")) return nullptr;
+  const double elapsed =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - g->wall0).count();
+  rngi::prof_clear(g->prof);
+  for (const OpRec &op : g->ops) {
+    float t0 = 0.f, t1 = 0.f;
+    st = cudaEventElapsedTime(&t0, g->origin, g->evpool[op.ev0]);
+    if (st == cudaSuccess) st = cudaEventElapsedTime(&t1, g->origin, g->evpool[op.ev1]);
+    if (st != cudaSuccess) {
+      rngi::cuda_fail(err, st, "cudaEventElapsedTime");
+      return nullptr;
+    }
+    rngi::prof_add(g->prof, op.queue, op.name, t0 * 1e-3, t1 * 1e-3);
+  }
+  rng_prof_set_elapsed(g->prof, elapsed);
+  if (rng_prof_calc(g->prof, err)) return nullptr;
+  return g->prof;
+}
+
+const char *rng_profile_summary(rng_gen *g, int agg_sort, int ovl_sort, rng_err **err) {
+  rng_prof *p = rng_profiler(g, err);
+  if (!p) return nullptr;
+  const char *s = rng_prof_summary(p, agg_sort, ovl_sort);
+  g->summary = s ? s : "";
+  return g->summary.c_str();
+}
+
+int rng_profile_export(rng_gen *g, const char *path, rng_err **err) {
+  rng_prof *p = rng_profiler(g, err);
+  if (!p) return err && *err ? (*err)->code : RNG_ECUDA;
+  return rng_prof_export(p, path, err);
+}
+
+int rng_profile_reset(rng_gen *g, rng_err **err) {
+  int rc = check_gen(g, err, "rng_profile_reset");
+  if (rc) return rc;
+  return profile_restart(g, err);
+}
+
+int rng_profile_stat(rng_gen *g, const char *name, uint64_t *count, double *total_s, rng_err **err) {
+  int rc = check_gen(g, err, "rng_profile_stat");
+  if (rc) return rc;
+  if (!name) return rngi::fail(err, RNG_EINVAL, "rng_profile_stat: NULL name");
+  uint64_t n = 0;
+  double tot = 0.0;
+  bool synced = false;
+  for (const OpRec &op : g->ops) {
+    if (strcmp(op.name, name) != 0) continue;
+    if (!synced) {
+      cudaError_t st = cudaEventSynchronize(g->evpool[g->ops.back().ev1]);
+      if (st == cudaSuccess) st = cudaStreamSynchronize(g->compute);
+      if (st == cudaSuccess) st = cudaStreamSynchronize(g->copy);
+      rc = rngi::cuda_fail(err, st, "rng_profile_stat: synchronize");
+      if (rc) return rc;
+      synced = true;
+    }
+    float ms = 0.f;
+    cudaError_t st = cudaEventElapsedTime(&ms, g->evpool[op.ev0], g->evpool[op.ev1]);
+    rc = rngi::cuda_fail(err, st, "cudaEventElapsedTime");
+    if (rc) return rc;
+    ++n;
+    tot += ms * 1e-3;
+  }
+  if (count) *count = n;
+  if (total_s) *total_s = tot;
+  return RNG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,401 @@
+// GPU kernels of the massive PRNG (Section 5 of the cf4ocl paper) for sm_103a.
+//
+// The paper's rng kernel reads a state, applies one xorshift update and
+// writes one value per work-item per launch, with the host swapping two
+// buffers between launches.  Here one launch covers many iterations: each
+// thread keeps its streams' states in registers for the whole launch and
+// writes one row (iteration) after another in the iteration-major layout,
+// with warp-contiguous 16-byte stores.  Nothing is read per value; the
+// state array is touched once at the start and once at the end.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "prng_math.cuh"
+
+namespace rngi {
+namespace {
+
+constexpr int kPolicyDefault = 0;
+constexpr int kPolicyStreaming = 1;
+
+template <int POLICY>
+__device__ __forceinline__ void store_pair(uint64_t *p, uint64_t a, uint64_t b) {
+  if (POLICY == kPolicyStreaming)
+    asm volatile("st.global.cs.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+  else
+    asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+template <int POLICY>
+__device__ __forceinline__ void store_one(uint64_t *p, uint64_t a) {
+  if (POLICY == kPolicyStreaming)
+    asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+  else
+    asm volatile("st.global.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
+
+// Stream offset (within a tile) of value q of store slot j for thread t:
+// slot j of all threads of the block forms one contiguous run of
+// blockDim * P values, so every warp-wide store is 32 * 8 * P contiguous bytes.
+constexpr int kBlock = 256;  // threads per block of every generation kernel
+
+template <int P>
+__device__ __forceinline__ uint64_t slot_offset(int j, int q) {
+  return static_cast<uint64_t>(P) * (threadIdx.x + static_cast<uint64_t>(kBlock) * j) + q;
+}
+
+// Emits `rows` rows of one tile.  CHECK: some values of the tile lie past
+// the end of the stream range and must not be stored.
+template <int VPT, bool VEC, int POLICY, bool CHECK>
+__device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, uint64_t pitch,
+                                          uint64_t rows, uint64_t rel0, uint64_t span) {
+  constexpr int P = VEC ? 2 : 1;
+  constexpr int J = VPT / P;
+  for (uint64_t r = 0; r < rows; ++r, row += pitch) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const uint64_t rel = rel0 + slot_offset<P>(j, 0);
+      if (VEC) {
+        if (!CHECK || rel + 1 < span)
+          store_pair<POLICY>(row + rel, st[2 * j], st[2 * j + 1]);
+        else if (rel < span)
+          store_one<POLICY>(row + rel, st[2 * j]);
+      } else {
+        if (!CHECK || rel < span) store_one<POLICY>(row + rel, st[j]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+  }
+}
+
+template <int VPT, bool VEC>
+__device__ __forceinline__ void load_tile(uint64_t (&st)[VPT], const RowsLaunch &a, uint64_t rel0,
+                                          uint64_t span) {
+  constexpr int P = VEC ? 2 : 1;
+#pragma unroll
+  for (int j = 0; j < VPT / P; ++j)
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const uint64_t rel = rel0 + slot_offset<P>(j, q);
+      const uint64_t s = a.s_begin + rel;
+      uint64_t v = 0;
+      if (rel < span) v = a.from_hash ? prng::initial_state(a.id_base + s, a.key) : a.state[s];
+      st[j * P + q] = v;
+    }
+}
+
+template <int VPT, bool VEC>
+__device__ __forceinline__ void store_tile_state(const uint64_t (&st)[VPT], const RowsLaunch &a,
+                                                 uint64_t rel0, uint64_t span) {
+  constexpr int P = VEC ? 2 : 1;
+#pragma unroll
+  for (int j = 0; j < VPT / P; ++j)
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const uint64_t rel = rel0 + slot_offset<P>(j, q);
+      if (rel < span) a.state[a.s_begin + rel] = st[j * P + q];
+    }
+}
+
+// Persistent row kernel: blocks walk the tiles of blockDim * VPT streams;
+// each thread holds VPT states in registers across all rows of its tile.
+template <int VPT, bool VEC, int POLICY>
+__global__ void __launch_bounds__(kBlock) rows_kernel(const RowsLaunch a) {
+  const uint64_t span = a.s_end - a.s_begin;
+  const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
+  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const uint64_t rel0 = tile * tile_vals;
+    uint64_t st[VPT];
+    load_tile<VPT, VEC>(st, a, rel0, span);
+    if (a.out) {
+      if (rel0 + tile_vals <= span)
+        emit_rows<VPT, VEC, POLICY, false>(st, a.out, a.pitch, a.rows, rel0, span);
+      else
+        emit_rows<VPT, VEC, POLICY, true>(st, a.out, a.pitch, a.rows, rel0, span);
+    } else {
+      for (uint64_t r = 0; r < a.rows; ++r)
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+    }
+    if (a.write_state) store_tile_state<VPT, VEC>(st, a, rel0, span);
+  }
+}
+
+// Separate init kernel (Listing S4): state[s] = initial state of id_base + s.
+__global__ void init_kernel(uint64_t *__restrict__ state, uint64_t n, uint64_t id_base,
+                            uint32_t key) {
+  for (uint64_t s = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    state[s] = prng::initial_state(id_base + s, key);
+}
+
+// 64-bit XOR and wrapping sum across a warp with 32-bit reductions: the sum
+// is split into two 16-bit low parts (no carry can be lost over 32 lanes)
+// and the high word, whose sum only matters modulo 2^32.
+__device__ __forceinline__ void warp_xor_sum(uint64_t &x, uint64_t &s) {
+  const unsigned full = 0xffffffffu;
+  const uint32_t xl = __reduce_xor_sync(full, static_cast<uint32_t>(x));
+  const uint32_t xh = __reduce_xor_sync(full, static_cast<uint32_t>(x >> 32));
+  const uint32_t lo = static_cast<uint32_t>(s);
+  const uint32_t a = __reduce_add_sync(full, lo & 0xffffu);
+  const uint32_t b = __reduce_add_sync(full, lo >> 16);
+  const uint32_t c = __reduce_add_sync(full, static_cast<uint32_t>(s >> 32));
+  x = (static_cast<uint64_t>(xh) << 32) | xl;
+  s = static_cast<uint64_t>(a) + (static_cast<uint64_t>(b) << 16) + (static_cast<uint64_t>(c) << 32);
+}
+
+// Generate-and-checksum: per row, XOR and sum of all values of the launch's
+// stream range, reduced per warp, then per block (double-buffered shared
+// slots, one barrier per row), then one atomic pair per block and row.
+template <int VPT>
+__global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
+                                                       unsigned long long *row_xor,
+                                                       unsigned long long *row_sum) {
+  __shared__ uint64_t sx[2][kBlock / 32], ss[2][kBlock / 32];
+  const uint64_t span = a.s_end - a.s_begin;
+  const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int n_warps = kBlock / 32;
+  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const uint64_t rel0 = tile * tile_vals;
+    uint64_t st[VPT];
+    load_tile<VPT, false>(st, a, rel0, span);
+    for (uint64_t r = 0; r < a.rows; ++r) {
+      uint64_t x = 0, s = 0;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        x ^= st[v];
+        s += st[v];
+        st[v] = prng::xorshift_update(st[v]);
+      }
+      warp_xor_sum(x, s);
+      const int buf = static_cast<int>(r & 1);
+      if (lane == 0) {
+        sx[buf][warp] = x;
+        ss[buf][warp] = s;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        uint64_t bx = lane < n_warps ? sx[buf][lane] : 0;
+        uint64_t bs = lane < n_warps ? ss[buf][lane] : 0;
+        warp_xor_sum(bx, bs);
+        if (lane == 0) {
+          atomicXor(row_xor + r, static_cast<unsigned long long>(bx));
+          atomicAdd(row_sum + r, static_cast<unsigned long long>(bs));
+        }
+      }
+    }
+    // Values past the end of the range were loaded as 0 and advance to 0,
+    // so they add nothing; the states of real streams are written back.
+    if (a.write_state) store_tile_state<VPT, false>(st, a, rel0, span);
+    __syncthreads();
+  }
+}
+
+// Batched persistent kernel: blocks take work units (instance, tile of
+// streams) from a shared counter, largest units first, and emit all rows of
+// the unit from the hash of the ids (every instance starts at iteration 0).
+template <int VPT>
+__global__ void __launch_bounds__(kBlock) batch_kernel(const BatchInstance *__restrict__ inst,
+                                                    const BatchUnit *__restrict__ units,
+                                                    uint32_t n_units, uint32_t *counter) {
+  __shared__ uint32_t s_unit;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t u = s_unit;
+    __syncthreads();
+    if (u >= n_units) return;
+    const BatchUnit wu = units[u];
+    const BatchInstance in = inst[wu.inst];
+    RowsLaunch a;
+    a.state = nullptr;
+    a.out = in.out;
+    a.pitch = in.streams;
+    a.s_begin = wu.s_begin;
+    a.s_end = wu.s_begin + wu.count;
+    a.id_base = 0;
+    a.rows = in.rows;
+    a.key = in.key;
+    a.from_hash = 1;
+    a.write_state = 0;
+    const uint64_t span = wu.count;
+    const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+    uint64_t *row = in.out + wu.s_begin;
+    if (in.vec && (VPT % 2 == 0)) {
+      constexpr int V2 = VPT >= 2 ? VPT : 2;
+      uint64_t st[V2];
+      load_tile<V2, true>(reinterpret_cast<uint64_t(&)[V2]>(st), a, 0, span);
+      if (span == tile_vals)
+        emit_rows<V2, true, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
+      else
+        emit_rows<V2, true, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+    } else {
+      uint64_t st[VPT];
+      load_tile<VPT, false>(st, a, 0, span);
+      if (span == tile_vals)
+        emit_rows<VPT, false, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
+      else
+        emit_rows<VPT, false, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+    }
+  }
+}
+
+template <int VPT, bool VEC, int POLICY>
+const void *rows_fn() {
+  return reinterpret_cast<const void *>(&rows_kernel<VPT, VEC, POLICY>);
+}
+
+template <int VPT>
+const void *rows_fn_dispatch(bool vec, int policy) {
+  if (VPT >= 2 && vec) {
+    constexpr int V = VPT >= 2 ? VPT : 2;
+    return policy == kPolicyStreaming ? rows_fn<V, true, kPolicyStreaming>()
+                                      : rows_fn<V, true, kPolicyDefault>();
+  }
+  return policy == kPolicyStreaming ? rows_fn<VPT, false, kPolicyStreaming>()
+                                    : rows_fn<VPT, false, kPolicyDefault>();
+}
+
+const void *select_rows(uint32_t vpt, bool vec, int policy) {
+  switch (vpt) {
+    case 1: return rows_fn_dispatch<1>(false, policy);
+    case 2: return rows_fn_dispatch<2>(vec, policy);
+    case 4: return rows_fn_dispatch<4>(vec, policy);
+    case 8: return rows_fn_dispatch<8>(vec, policy);
+    case 16: return rows_fn_dispatch<16>(vec, policy);
+    case 32: return rows_fn_dispatch<32>(vec, policy);
+    case 64: return rows_fn_dispatch<64>(vec, policy);
+    default: return nullptr;
+  }
+}
+
+const void *select_checksum(uint32_t vpt) {
+  switch (vpt) {
+    case 1: return reinterpret_cast<const void *>(&checksum_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&checksum_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&checksum_kernel<4>);
+    case 8: return reinterpret_cast<const void *>(&checksum_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&checksum_kernel<16>);
+    case 32: return reinterpret_cast<const void *>(&checksum_kernel<32>);
+    case 64: return reinterpret_cast<const void *>(&checksum_kernel<64>);
+    default: return nullptr;
+  }
+}
+
+const void *select_batch(uint32_t vpt) {
+  switch (vpt) {
+    case 1: return reinterpret_cast<const void *>(&batch_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&batch_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&batch_kernel<4>);
+    case 8: return reinterpret_cast<const void *>(&batch_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&batch_kernel<16>);
+    case 32: return reinterpret_cast<const void *>(&batch_kernel<32>);
+    default: return nullptr;
+  }
+}
+
+int occupancy(const void *fn, uint32_t block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, static_cast<int>(block), 0) !=
+          cudaSuccess ||
+      n < 1)
+    n = 1;
+  return n;
+}
+
+}  // namespace
+
+int device_sm_count(int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+    sms = 1;
+  return sms;
+}
+
+LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device) {
+  LaunchShape sh;
+  (void)block;
+  sh.block = kBlock;
+  const int sms = device_sm_count(device);
+  if (vpt == 0) {
+    // Largest values-per-thread (<= 16) that still gives every SM at least
+    // 1024 threads of work; small runs fall back to one stream per thread.
+    vpt = 1;
+    const uint64_t want_threads = static_cast<uint64_t>(sms) * 1024;
+    for (uint32_t v = 16; v >= 2; v /= 2)
+      if (streams / v >= want_threads) {
+        vpt = v;
+        break;
+      }
+  }
+  sh.vpt = vpt;
+  const void *fn = select_rows(vpt, vpt >= 2, kPolicyDefault);
+  const uint64_t tiles = (streams + static_cast<uint64_t>(sh.block) * vpt - 1) /
+                         (static_cast<uint64_t>(sh.block) * vpt);
+  const uint64_t resident = static_cast<uint64_t>(sms) * occupancy(fn, sh.block);
+  uint64_t grid = tiles < resident ? tiles : resident;
+  sh.grid = static_cast<uint32_t>(grid ? grid : 1);
+  return sh;
+}
+
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy,
+                        cudaStream_t st) {
+  const bool vec = sh.vpt >= 2 && a.out && (a.pitch % 2 == 0) &&
+                   (reinterpret_cast<uintptr_t>(a.out) % 16 == 0);
+  const void *fn = select_rows(sh.vpt, vec, store_policy);
+  if (!fn || sh.block != kBlock) return cudaErrorInvalidValue;
+  RowsLaunch args = a;
+  void *params[] = {&args};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
+                        cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t blocks_needed = (n + 255) / 256;
+  const uint64_t cap = static_cast<uint64_t>(device_sm_count(dev)) * 8;
+  const unsigned grid = static_cast<unsigned>(blocks_needed < cap ? blocks_needed : cap);
+  init_kernel<<<grid ? grid : 1, 256, 0, st>>>(state, n, id_base, key);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+cudaError_t launch_checksum(const RowsLaunch &a, const LaunchShape &sh, uint64_t *row_xor,
+                            uint64_t *row_sum, cudaStream_t st) {
+  const void *fn = select_checksum(sh.vpt);
+  if (!fn || sh.block != kBlock) return cudaErrorInvalidValue;
+  RowsLaunch args = a;
+  unsigned long long *rx = reinterpret_cast<unsigned long long *>(row_xor);
+  unsigned long long *rs = reinterpret_cast<unsigned long long *>(row_sum);
+  void *params[] = {&args, &rx, &rs};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+int batch_blocks_per_sm(uint32_t vpt, uint32_t block) {
+  const void *fn = select_batch(vpt);
+  return fn ? occupancy(fn, block) : 0;
+}
+
+cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint32_t n_units,
+                         uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
+                         cudaStream_t st) {
+  const void *fn = select_batch(vpt);
+  if (!fn || block != kBlock) return cudaErrorInvalidValue;
+  void *params[] = {&inst, &units, &n_units, &counter};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+}  // namespace rngi

@@ -1,0 +1,279 @@
+"""Python face of the generator object (Section 5 of the cf4ocl paper).
+
+PyTorch supplies device memory and streams; every value is produced by the
+CUDA library behind ``include/rng.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Callable, Optional
+
+import numpy as np
+import torch
+
+from . import _capi as C
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Generator:
+    """``streams`` independent xorshift streams seeded by the id hash.
+
+    ``generate(T)`` returns the next ``T`` iterations as a ``(T, streams)``
+    uint64 CUDA tensor (iteration-major, value ``[i, g]``); iteration 0 is the
+    init value.  ``generate_to_host`` streams the same values into host
+    memory through the double-buffered copy path.
+    """
+
+    def __init__(self, streams: int, seed: int = 0, *, values_per_thread: int = 0,
+                 fuse_init: bool = True, stream_offset: int = 0,
+                 device_buffer_bytes: int = 32 << 20, host_slots: int = 2,
+                 profiling: bool = True, compute_stream=None, device: Optional[int] = None,
+                 store_policy: int = 0, host_wait_ms: int = 0, init: bool = True):
+        lib = C.load()
+        o = C.RngOpts()
+        lib.rng_opts_default(ctypes.byref(o))
+        o.values_per_thread = values_per_thread
+        o.fuse_init = 1 if fuse_init else 0
+        o.stream_offset = stream_offset
+        o.device_buffer_bytes = device_buffer_bytes
+        o.host_slots = host_slots
+        o.profiling = 1 if profiling else 0
+        h = _stream_handle(compute_stream)
+        o.compute_stream = h
+        o.device = -1 if device is None else device
+        o.store_policy = store_policy
+        o.host_wait_ms = host_wait_ms
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            C.check(lib.rng_create, streams, seed & ((1 << 64) - 1), ctypes.byref(o), ctypes.byref(self._h))
+        self.streams = streams
+        self.seed = seed
+        if init:
+            self.init()
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if self._h:
+            self._lib.rng_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- generation ------------------------------------------------------------
+    def init(self):
+        C.check(self._lib.rng_init, self._h)
+
+    @property
+    def position(self) -> int:
+        p = ctypes.c_uint64()
+        self._lib.rng_position(self._h, ctypes.byref(p))
+        return p.value
+
+    @property
+    def stream(self) -> torch.cuda.ExternalStream:
+        return torch.cuda.ExternalStream(self._lib.rng_compute_stream(self._h), device=self.device)
+
+    def launch_config(self):
+        v, b, g = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        self._lib.rng_launch_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(g))
+        return v.value, b.value, g.value
+
+    def generate(self, iterations: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Next ``iterations`` rows on the device (asynchronous on the
+        generator's compute stream)."""
+        if out is None:
+            out = torch.empty((iterations, self.streams), dtype=torch.uint64, device=self.device)
+        assert out.is_cuda and out.is_contiguous() and out.element_size() == 8
+        assert out.numel() >= iterations * self.streams
+        # Order the write after the tensor's allocation on torch's stream.
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(self.device))
+        self.stream.wait_event(ev)
+        C.check(self._lib.rng_generate, self._h, iterations, ctypes.c_void_p(out.data_ptr()), None)
+        out.record_stream(self.stream)
+        return out
+
+    def generate_to(self, iterations: int, out_ptr: int):
+        """Raw form: ``out_ptr`` is a device address of 8*streams*iterations bytes."""
+        C.check(self._lib.rng_generate, self._h, iterations, ctypes.c_void_p(out_ptr), None)
+
+    def generate_to_host(self, iterations: int, out=None):
+        """Next ``iterations`` rows into host memory (blocks until done).
+
+        ``out`` may be a numpy uint64 array or a CPU tensor (pinned memory is
+        written directly by the copy engine)."""
+        if out is None:
+            out = np.empty((iterations, self.streams), dtype=np.uint64)
+        if isinstance(out, torch.Tensor):
+            assert out.device.type == "cpu" and out.is_contiguous() and out.element_size() == 8
+            ptr = out.data_ptr()
+            n = out.numel()
+        else:
+            assert out.dtype == np.uint64 and out.flags.c_contiguous
+            ptr = out.ctypes.data
+            n = out.size
+        assert n >= iterations * self.streams
+        C.check(self._lib.rng_generate, self._h, iterations, None, ctypes.c_void_p(ptr))
+        return out
+
+    def generate_sink(self, iterations: int, sink: Callable[[int, np.ndarray, int], Optional[int]]):
+        """Streams ``iterations`` rows through the pinned staging slots and
+        calls ``sink(first_iteration, block, first_stream)`` per chunk, where
+        ``block`` is a ``(rows, n_streams)`` uint64 view valid only during the
+        call.  A truthy return value stops the run."""
+        failure = []
+
+        def _cb(_user, first_it, rows, first_stream, n_streams, pitch, values):
+            try:
+                buf = np.ctypeslib.as_array(values, shape=(rows * pitch,))
+                block = buf.reshape(rows, pitch)[:, :n_streams]
+                r = sink(int(first_it), block, int(first_stream))
+                return int(r) if r else 0
+            except Exception as e:  # surface Python errors as a sink failure
+                failure.append(e)
+                return 1
+
+        cb = C.SINK_FN(_cb)
+        try:
+            C.check(self._lib.rng_generate_sink, self._h, iterations, cb, None)
+        except C.RngError:
+            if failure:
+                raise failure[0]
+            raise
+
+    def generate_checksum(self, iterations: int, row_xor: Optional[torch.Tensor] = None,
+                          row_sum: Optional[torch.Tensor] = None):
+        """Per-iteration XOR and wrapping sum over all streams, without
+        storing the values (two uint64 CUDA tensors of length ``iterations``)."""
+        if row_xor is None:
+            row_xor = torch.empty(iterations, dtype=torch.uint64, device=self.device)
+        if row_sum is None:
+            row_sum = torch.empty(iterations, dtype=torch.uint64, device=self.device)
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(self.device))
+        self.stream.wait_event(ev)
+        C.check(self._lib.rng_generate_checksum, self._h, iterations,
+                ctypes.c_void_p(row_xor.data_ptr()), ctypes.c_void_p(row_sum.data_ptr()))
+        row_xor.record_stream(self.stream)
+        row_sum.record_stream(self.stream)
+        return row_xor, row_sum
+
+    def state(self) -> np.ndarray:
+        out = np.empty(self.streams, dtype=np.uint64)
+        C.check(self._lib.rng_get_state, self._h, ctypes.c_void_p(out.ctypes.data))
+        return out
+
+    def sync(self):
+        C.check(self._lib.rng_sync, self._h)
+
+    # -- profiling -------------------------------------------------------------
+    def profile_summary(self, agg_sort=C.RNG_PROF_SORT_TIME | C.RNG_PROF_SORT_DESC,
+                        ovl_sort=C.RNG_PROF_SORT_TIME | C.RNG_PROF_SORT_DESC) -> str:
+        err = ctypes.POINTER(C.RngErr)()
+        s = self._lib.rng_profile_summary(self._h, agg_sort, ovl_sort, ctypes.byref(err))
+        if not s:
+            msg = err.contents.msg.decode() if err else "rng_profile_summary failed"
+            self._lib.rng_err_clear(ctypes.byref(err))
+            raise C.RngError(C.RNG_ECUDA, msg)
+        return s.decode()
+
+    def profile_export(self, path: str):
+        C.check(self._lib.rng_profile_export, self._h, path.encode())
+
+    def profile_reset(self):
+        C.check(self._lib.rng_profile_reset, self._h)
+
+    def profile_stat(self, name: str):
+        """(count, summed device seconds) of the recorded events ``name``."""
+        n, t = ctypes.c_uint64(), ctypes.c_double()
+        C.check(self._lib.rng_profile_stat, self._h, name.encode(), ctypes.byref(n), ctypes.byref(t))
+        return n.value, t.value
+
+    def profile(self):
+        """Analysed profile: dict with aggregates, overlaps, totals."""
+        err = ctypes.POINTER(C.RngErr)()
+        p = self._lib.rng_profiler(self._h, ctypes.byref(err))
+        if not p:
+            msg = err.contents.msg.decode() if err else "rng_profiler failed"
+            self._lib.rng_err_clear(ctypes.byref(err))
+            raise C.RngError(C.RNG_ECUDA, msg)
+        return Profiler._read(self._lib, p)
+
+
+class Profiler:
+    """Stand-alone profiler over explicit intervals (host only)."""
+
+    def __init__(self):
+        self._lib = C.load()
+        self._h = self._lib.rng_prof_new()
+        if not self._h:
+            raise MemoryError("rng_prof_new failed")
+
+    def add(self, queue: str, name: str, start_s: float, end_s: float):
+        rc = self._lib.rng_prof_add(self._h, queue.encode(), name.encode(), start_s, end_s)
+        if rc != C.RNG_OK:
+            raise C.RngError(rc, "rng_prof_add rejected the event")
+
+    def set_elapsed(self, s: float):
+        self._lib.rng_prof_set_elapsed(self._h, s)
+
+    def calc(self):
+        C.check(self._lib.rng_prof_calc, self._h)
+        return Profiler._read(self._lib, self._h)
+
+    def summary(self, agg_sort=C.RNG_PROF_SORT_TIME | C.RNG_PROF_SORT_DESC,
+                ovl_sort=C.RNG_PROF_SORT_TIME | C.RNG_PROF_SORT_DESC) -> str:
+        return self._lib.rng_prof_summary(self._h, agg_sort, ovl_sort).decode()
+
+    def export(self, path: str):
+        C.check(self._lib.rng_prof_export, self._h, path.encode())
+
+    def close(self):
+        if self._h:
+            self._lib.rng_prof_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _read(lib, h):
+        aggs = {}
+        for i in range(lib.rng_prof_num_aggregates(h)):
+            nm, a, r = C.c_cp(), C.c_dbl(), C.c_dbl()
+            lib.rng_prof_aggregate(h, i, ctypes.byref(nm), ctypes.byref(a), ctypes.byref(r))
+            aggs[nm.value.decode()] = (a.value, r.value)
+        ovl = {}
+        for i in range(lib.rng_prof_num_overlaps(h)):
+            n1, n2, d = C.c_cp(), C.c_cp(), C.c_dbl()
+            lib.rng_prof_overlap(h, i, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(d))
+            ovl[(n1.value.decode(), n2.value.decode())] = d.value
+        return {
+            "aggregate": aggs,
+            "overlaps": ovl,
+            "total": lib.rng_prof_total(h),
+            "effective": lib.rng_prof_effective(h),
+            "elapsed": lib.rng_prof_elapsed(h),
+        }

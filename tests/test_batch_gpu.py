@@ -1,0 +1,85 @@
+"""Batched form against the oracle, instance by instance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1609_01257_gb300 as rng
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_small_batch_fixed_vpt_all_values():
+    streams = [1, 2, 3, 255, 256, 257, 1000, 4099, 70_000]
+    iters = [1, 5, 2, 7, 3, 1, 9, 4, 2]
+    seeds = [0, 1, 2, 3, 4, 5, 6, 7, 2**64 - 1]
+    for vpt in (1, 2, 8, 32):
+        b = rng.Batch(streams, iters, seeds, values_per_thread=vpt)
+        b.run()
+        b.sync()
+        for k in range(len(streams)):
+            got = b.outputs[k].cpu().numpy()
+            assert np.array_equal(got, oracle.generate(streams[k], seeds[k], iters[k])), (vpt, k)
+        b.close()
+
+
+def test_replay_is_identical_and_autotuned():
+    streams = [3000, 5, 1 << 16]
+    iters = [3, 40, 6]
+    seeds = [10, 11, 12]
+    b = rng.Batch(streams, iters, seeds)
+    cfg = b.config()
+    assert cfg["values_per_thread"] in (1, 2, 4, 8, 16, 32) and cfg["tuned_ms"] > 0
+    for o in b.outputs:
+        o.view(torch.int64).zero_()
+    torch.cuda.synchronize()
+    b.run()
+    b.sync()
+    first = [o.cpu().numpy().copy() for o in b.outputs]
+    b.run()
+    b.sync()
+    for k, o in enumerate(b.outputs):
+        assert np.array_equal(o.cpu().numpy(), first[k])
+        assert np.array_equal(first[k], oracle.generate(streams[k], seeds[k], iters[k]))
+    b.close()
+
+
+def test_unaligned_instance_outputs():
+    # One shared buffer with instances at 8-byte (not 16-byte) offsets.
+    streams, iters, seeds = [6, 10, 4], [3, 2, 5], [1, 2, 3]
+    sizes = [n * t for n, t in zip(streams, iters)]
+    buf = torch.zeros(sum(sizes) + 1, dtype=torch.int64, device="cuda").view(torch.uint64)
+    outs, off = [], 1
+    for s, n, t in zip(sizes, streams, iters):
+        outs.append(buf[off:off + s].view(t, n))
+        off += s
+    b = rng.Batch(streams, iters, seeds, outputs=outs, values_per_thread=4)
+    b.run()
+    b.sync()
+    for k in range(3):
+        assert np.array_equal(outs[k].cpu().numpy(), oracle.generate(streams[k], seeds[k], iters[k]))
+    assert int(buf.view(torch.int64)[0].item()) == 0
+    b.close()
+
+
+def test_paper_shaped_batch_sampled():
+    # 512 instances, log-uniform sizes, 8 GiB total: every instance checked on
+    # its first row and sampled values, small instances in full.
+    inst = workloads.batched_instances()
+    b = rng.Batch([i.streams for i in inst], [i.iterations for i in inst], [i.seed for i in inst])
+    b.run()
+    b.sync()
+    rs = np.random.default_rng(0)
+    for k, ins in enumerate(inst):
+        out = b.outputs[k]
+        if ins.streams * ins.iterations <= 200_000:
+            assert np.array_equal(out.cpu().numpy(), oracle.generate(ins.streams, ins.seed, ins.iterations)), k
+            continue
+        row0 = out[0].cpu().numpy()
+        assert np.array_equal(row0, oracle.generate(ins.streams, ins.seed, 1)[0]), k
+        last = out[ins.iterations - 1].cpu().numpy()
+        gs = rs.integers(0, ins.streams, 16)
+        for g in gs:
+            assert int(last[g]) == oracle.value(int(g), ins.seed, ins.iterations - 1)
+    b.close()

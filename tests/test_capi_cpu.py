@@ -1,0 +1,159 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every
+declared symbol, rejects bad arguments with status codes (no exit, no
+crash), and its host-only profiler reproduces the paper's summary."""
+import ctypes
+import os
+import random
+import re
+
+import pytest
+
+import paper_1609_01257_gb300 as lib
+from paper_1609_01257_gb300 import _capi as C
+from oracle import profile as oprof
+from tests import golden_profile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "rng.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(rng_[a-z_0-9]+)\s*\(", src))
+    names.discard("rng_sink_fn")
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    lib.build()
+    return lib.load()
+
+
+def test_every_declared_symbol_is_exported(L):
+    declared = _declared_functions()
+    assert len(declared) >= 40
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert declared == set(C.SIGNATURES), declared ^ set(C.SIGNATURES)
+
+
+def test_strerror_and_counters(L):
+    for code in range(8):
+        assert L.rng_strerror(code)
+    assert L.rng_strerror(99) == b"unknown status"
+    assert L.rng_live_objects() >= 0
+
+
+def test_bad_arguments_return_status_not_crash(L):
+    err = ctypes.POINTER(C.RngErr)()
+    h = ctypes.c_void_p()
+    rc = L.rng_create(0, 1, None, ctypes.byref(h), ctypes.byref(err))
+    assert rc == C.RNG_EINVAL and err and b"streams" in err.contents.msg
+    L.rng_err_clear(ctypes.byref(err))
+    assert not err
+    rc = L.rng_create((1 << 32) + 1, 1, None, ctypes.byref(h), None)
+    assert rc == C.RNG_EINVAL
+    o = C.RngOpts()
+    L.rng_opts_default(ctypes.byref(o))
+    o.values_per_thread = 3
+    assert L.rng_create(16, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL
+    o.values_per_thread = 0
+    o.struct_size = 4
+    assert L.rng_create(16, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL
+    assert L.rng_init(None, None) == C.RNG_EINVAL
+    assert L.rng_generate(None, 1, None, None, None) == C.RNG_EINVAL
+    L.rng_destroy(None)
+    L.rng_batch_destroy(None)
+    L.rng_prof_destroy(None)
+    assert L.rng_batch_create(0, None, None, None, None, None, ctypes.byref(h), None) == C.RNG_EINVAL
+
+
+def test_create_without_gpu_fails_cleanly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    h = ctypes.c_void_p()
+    err = ctypes.POINTER(C.RngErr)()
+    before = L.rng_live_objects()
+    rc = L.rng_create(16, 1, None, ctypes.byref(h), ctypes.byref(err))
+    assert rc in (C.RNG_ECUDA, C.RNG_ENOMEM)
+    assert not h
+    assert L.rng_live_objects() == before
+    L.rng_err_clear(ctypes.byref(err))
+
+
+def test_library_profiler_reproduces_paper_summary(L):
+    fx = golden_profile.load()
+    p = lib.Profiler()
+    for q, n, s, e in golden_profile.synthetic_events(fx):
+        p.add(q, n, s, e)
+    p.set_elapsed(fx["elapsed"])
+    a = p.calc()
+    for name, (rel, abs_s) in fx["agg"].items():
+        assert a["aggregate"][name][0] == pytest.approx(abs_s, rel=1e-9)
+        assert a["aggregate"][name][1] == pytest.approx(rel, abs=2e-3)
+    assert a["overlaps"] == {("RNG_KERNEL", "READ_BUFFER"): pytest.approx(fx["overlap_total"], rel=1e-9)}
+    assert a["effective"] == pytest.approx(fx["effective"], abs=5e-5)
+    s = p.summary()
+    # Lines of the printed figure, at its precision.
+    assert re.search(r"\| READ_BUFFER\s+\|\s+89\.08\d\d \|\s+6\.6521e\+00 \|", s), s
+    assert re.search(r"\| RNG_KERNEL\s+\|\s+10\.918\d \|\s+8\.1531e-01 \|", s), s
+    assert re.search(r"\| INIT_KERNEL\s+\|\s+0\.0008 \|\s+6\.2464e-05 \|", s), s
+    assert re.search(r"\| RNG_KERNEL\s+\| READ_BUFFER\s+\|\s+1\.5790e-02 \|", s), s
+    assert "Time spent in device      : 82.30%" in s
+    assert "Time spent in host        : 17.70%" in s
+    # Sorted by time, descending: READ first.
+    assert s.index("READ_BUFFER") < s.index("RNG_KERNEL") < s.index("INIT_KERNEL")
+    p.close()
+
+
+def test_library_profiler_matches_oracle_on_random_events(L, tmp_path):
+    rng = random.Random(5)
+    for trial in range(30):
+        evs = []
+        for q in ("Main", "Comms", "Aux")[: rng.randint(1, 3)]:
+            t = rng.random()
+            for _ in range(rng.randint(0, 12)):
+                d = rng.random() * 0.3
+                evs.append((q, rng.choice(["RNG_KERNEL", "READ_BUFFER", "INIT_KERNEL"]), t, t + d))
+                t += d + rng.random() * 0.1
+        rng.shuffle(evs)
+        p = lib.Profiler()
+        for e in evs:
+            p.add(*e)
+        p.set_elapsed(10.0)
+        got = p.calc()
+        want = oprof.analyse([oprof.Event(*e) for e in evs], 10.0)
+        assert set(got["aggregate"]) == set(want.aggregate)
+        for k, (a, r) in got["aggregate"].items():
+            assert a == pytest.approx(want.aggregate[k], abs=1e-12)
+            assert r == pytest.approx(want.relative[k], abs=1e-9)
+        assert set(got["overlaps"]) == set(want.overlaps)
+        for k, v in got["overlaps"].items():
+            assert v == pytest.approx(want.overlaps[k], abs=1e-12)
+        assert got["effective"] == pytest.approx(want.effective, abs=1e-12)
+        if trial == 0:
+            path = tmp_path / "ev.tsv"
+            p.export(str(path))
+            rows = [l.split("\t") for l in path.read_text().splitlines()]
+            assert len(rows) == len(evs)
+            starts = [float(r[1]) for r in rows]
+            assert starts == sorted(starts)
+        p.close()
+
+
+def test_profiler_rejects_inverted_interval(L):
+    p = lib.Profiler()
+    with pytest.raises(C.RngError):
+        p.add("Main", "X", 2.0, 1.0)
+    p.close()
+
+
+@pytest.mark.parametrize("total,world", [(10, 3), (1 << 22, 2), (7, 7), (5, 8)])
+def test_shard_range_partitions(total, world):
+    seen = []
+    for r in range(world):
+        first, count = lib.shard_range(total, r, world)
+        seen.extend(range(first, first + count))
+    assert seen == list(range(total))

@@ -1,0 +1,267 @@
+"""GPU path against the CPU oracle, element by element (bit-exact: all of
+the generator's arithmetic is integer)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1609_01257_gb300 as rng
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def dev_gen(n, seed, T, **kw):
+    g = rng.Generator(n, seed, **kw)
+    out = g.generate(T)
+    g.sync()
+    res = out.cpu().numpy()
+    g.close()
+    return res
+
+
+def test_plain_method_full_compare():
+    # 2^16 streams x 100 iterations, seed 0, device-resident: every value.
+    cfg = workloads.PLAIN
+    got = dev_gen(cfg["streams"], cfg["seed"], cfg["iterations"])
+    want = oracle.generate(cfg["streams"], cfg["seed"], cfg["iterations"])
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+    assert (got != 0).all()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 31, 33, 255, 257, 1023, 1025, 4095, 4097, 65535, 65537])
+@pytest.mark.parametrize("T", [1, 3, 17])
+def test_ragged_sizes(n, T):
+    got = dev_gen(n, 12345, T)
+    assert np.array_equal(got, oracle.generate(n, 12345, T))
+
+
+@pytest.mark.parametrize("vpt", [1, 2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("n", [4096 * 3 + 2, 100_001])
+def test_values_per_thread_variants(vpt, n):
+    got = dev_gen(n, 99, 9, values_per_thread=vpt)
+    assert np.array_equal(got, oracle.generate(n, 99, 9))
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_store_policies(policy):
+    got = dev_gen(70_000, 3, 11, store_policy=policy)
+    assert np.array_equal(got, oracle.generate(70_000, 3, 11))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 12345, 2**64 - 1, 0x9E3779B97F4A7C15])
+def test_seeds(seed):
+    assert np.array_equal(dev_gen(5000, seed, 4), oracle.generate(5000, seed, 4))
+
+
+def test_continuation_equals_single_call():
+    g = rng.Generator(3001, 7)
+    a = g.generate(5).cpu().numpy()
+    b = g.generate(1).cpu().numpy()
+    c = g.generate(13).cpu().numpy()
+    assert g.position == 19
+    g.close()
+    want = oracle.generate(3001, 7, 19)
+    assert np.array_equal(np.concatenate([a, b, c]), want)
+
+
+def test_separate_init_kernel_equals_fused():
+    for fuse in (True, False):
+        g = rng.Generator(4099, 5, fuse_init=fuse)
+        st = g.state()  # initial states (iteration-0 values)
+        assert np.array_equal(st, oracle.generate(4099, 5, 1)[0])
+        out = g.generate(6).cpu().numpy()
+        assert np.array_equal(out, oracle.generate(4099, 5, 6))
+        assert np.array_equal(g.state(), oracle.generate(4099, 5, 1, p0=6)[0])
+        g.close()
+
+
+def test_reinit_restarts():
+    g = rng.Generator(1000, 11)
+    first = g.generate(4).cpu().numpy()
+    g.generate(3)
+    g.init()
+    again = g.generate(4).cpu().numpy()
+    g.close()
+    assert np.array_equal(first, again)
+
+
+def test_stream_offset_is_a_column_block():
+    n, off, T = 2000, 123_456, 5
+    got = dev_gen(n, 77, T, stream_offset=off)
+    assert np.array_equal(got, oracle.generate(n, 77, T, g0=off))
+
+
+def test_generate_before_init_is_an_error():
+    g = rng.Generator(10, 1, init=False)
+    with pytest.raises(rng.RngError) as e:
+        g.generate(2)
+    assert e.value.code == 4
+    g.close()
+
+
+def test_both_or_no_output_is_an_error():
+    import ctypes
+    from paper_1609_01257_gb300 import _capi as C
+    g = rng.Generator(10, 1)
+    L = C.load()
+    buf = torch.empty(40, dtype=torch.uint64, device="cuda")
+    host = np.empty(40, dtype=np.uint64)
+    assert L.rng_generate(g._h, 2, None, None, None) == C.RNG_EINVAL
+    assert L.rng_generate(g._h, 2, ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(host.ctypes.data), None) == C.RNG_EINVAL
+    assert L.rng_generate(g._h, 0, ctypes.c_void_p(buf.data_ptr()), None, None) == C.RNG_OK
+    g.close()
+
+
+def test_unaligned_device_output():
+    # 8-byte aligned but not 16: scalar-store path.
+    n, T = 1000, 7
+    g = rng.Generator(n, 2)
+    raw = torch.zeros(n * T + 1, dtype=torch.int64, device="cuda")
+    g.generate_to(T, raw.data_ptr() + 8)
+    g.sync()
+    got = raw.cpu().numpy().view(np.uint64)
+    g.close()
+    assert got[0] == 0
+    assert np.array_equal(got[1:].reshape(T, n), oracle.generate(n, 2, T))
+
+
+def test_no_write_outside_output():
+    # Canary words around the output region stay untouched.
+    n, T = 5003, 9
+    g = rng.Generator(n, 8)
+    pad = 64
+    raw = torch.full((n * T + 2 * pad,), 0xA5A5A5A5, dtype=torch.int64, device="cuda")
+    g.generate_to(T, raw.data_ptr() + pad * 8)
+    g.sync()
+    r = raw.cpu().numpy()
+    g.close()
+    assert (r[:pad] == 0xA5A5A5A5).all() and (r[-pad:] == 0xA5A5A5A5).all()
+    assert np.array_equal(r[pad:-pad].view(np.uint64).reshape(T, n), oracle.generate(n, 8, T))
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("n,T,buf", [(4096, 40, 1 << 16), (3001, 7, 8 * 3001 * 2), (5000, 3, 4096), (7, 100, 64)])
+def test_host_output(pinned, n, T, buf):
+    # buf smaller than one row (5000 streams x 8 B > 4096) exercises column slabs.
+    g = rng.Generator(n, 4, device_buffer_bytes=buf)
+    out = torch.empty((T, n), dtype=torch.uint64)
+    if pinned:
+        out = out.pin_memory()
+    g.generate_to_host(T, out)
+    first = out.numpy().copy()
+    second = g.generate_to_host(2)
+    assert g.position == T + 2
+    g.close()
+    want = oracle.generate(n, 4, T + 2)
+    assert np.array_equal(first, want[:T])
+    assert np.array_equal(second, want[T:])
+
+
+def test_device_then_host_then_device():
+    g = rng.Generator(2048, 9, device_buffer_bytes=8 * 2048 * 3)
+    a = g.generate(4).cpu().numpy()
+    b = g.generate_to_host(10)
+    c = g.generate(2).cpu().numpy()
+    g.close()
+    assert np.array_equal(np.concatenate([a, b, c]), oracle.generate(2048, 9, 16))
+
+
+def test_sink_receives_every_chunk_in_order():
+    n, T = 3000, 25
+    g = rng.Generator(n, 6, device_buffer_bytes=8 * n * 4, host_slots=3)
+    got = np.zeros((T, n), dtype=np.uint64)
+    seen = []
+
+    def sink(first_it, block, first_stream):
+        seen.append((first_it, block.shape[0], first_stream))
+        got[first_it:first_it + block.shape[0], first_stream:first_stream + block.shape[1]] = block
+
+    g.generate_sink(T, sink)
+    g.close()
+    assert [s[0] for s in seen] == sorted(s[0] for s in seen)
+    assert np.array_equal(got, oracle.generate(n, 6, T))
+
+
+def test_sink_error_stops_run():
+    g = rng.Generator(1000, 6, device_buffer_bytes=8 * 1000)
+    calls = []
+
+    def sink(first_it, block, first_stream):
+        calls.append(first_it)
+        return 1 if first_it == 3 else 0
+
+    with pytest.raises(rng.RngError) as e:
+        g.generate_sink(20, sink)
+    assert e.value.code == 7
+    assert calls[-1] == 3
+    # The run failed part-way: the generator must be re-initialised.
+    with pytest.raises(rng.RngError):
+        g.generate(1)
+    g.init()
+    assert np.array_equal(g.generate(2).cpu().numpy(), oracle.generate(1000, 6, 2))
+    g.close()
+
+
+def test_stalled_consumer_times_out():
+    import time
+    g = rng.Generator(512, 6, device_buffer_bytes=8 * 512, host_slots=2, host_wait_ms=200)
+
+    def slow(first_it, block, first_stream):
+        time.sleep(0.6)
+
+    with pytest.raises(rng.RngError) as e:
+        g.generate_sink(8, slow)
+    assert e.value.code == 5
+    g.close()
+
+
+@pytest.mark.parametrize("n,T", [(1, 5), (33, 7), (4097, 20), (262_147, 6)])
+def test_checksum_mode(n, T):
+    g = rng.Generator(n, 12)
+    rx, rs = g.generate_checksum(T)
+    g.sync()
+    rx, rs = rx.cpu().numpy(), rs.cpu().numpy()
+    tail = g.generate(2).cpu().numpy()  # state advanced by T
+    g.close()
+    wx, ws, _ = oracle.row_checksums(n, 12, T)
+    assert np.array_equal(rx, wx) and np.array_equal(rs, ws)
+    assert np.array_equal(tail, oracle.generate(n, 12, 2, p0=T))
+
+
+def test_profiler_names_and_overlap():
+    n = 1 << 18
+    g = rng.Generator(n, 1, device_buffer_bytes=8 * n, fuse_init=False)
+    g.profile_reset()
+    g.init()
+    g.generate_to_host(8)
+    p = g.profile()
+    s = g.profile_summary()
+    cnt_k, t_k = g.profile_stat("RNG_KERNEL")
+    cnt_r, t_r = g.profile_stat("READ_BUFFER")
+    g.close()
+    assert set(p["aggregate"]) == {"INIT_KERNEL", "RNG_KERNEL", "READ_BUFFER"}
+    assert cnt_k == 8 and cnt_r == 8 and t_k > 0 and t_r > 0
+    assert p["effective"] <= p["total"] + 1e-12
+    assert p["effective"] <= p["elapsed"]
+    assert "Aggregate times by event" in s and "Time spent in device" in s
+
+
+def test_live_objects_balance():
+    before = rng.live_objects()
+    gs = [rng.Generator(100, k) for k in range(3)]
+    assert rng.live_objects() == before + 3
+    for g in gs:
+        g.close()
+    assert rng.live_objects() == before
+
+
+def test_launch_counter_counts_kernels():
+    g = rng.Generator(1000, 1)
+    c0 = rng.launch_count()
+    g.generate(3)
+    g.generate(3)
+    g.sync()
+    assert rng.launch_count() == c0 + 2
+    g.close()

@@ -1,0 +1,70 @@
+"""Paper-shaped streaming run at full size: 2^22 streams x 1024 iterations,
+seed 12345, through two 32 MiB device buffers into 32 GiB of page-locked host
+memory -- the launch configuration the benchmark's end-to-end leg times.
+Every 16th iteration is compared in full with the oracle, and every
+iteration's XOR and wrapping sum over all 2^22 values."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1609_01257_gb300 as rng
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _row_checksums(block: np.ndarray):
+    x = np.bitwise_xor.reduce(block, axis=1)
+    s = block.sum(axis=1, dtype=np.uint64)  # numpy wraps modulo 2^64 for uint64
+    return x, s
+
+
+def test_streaming_full_size_sampled_rows_and_checksums():
+    cfg = workloads.STREAMING
+    n, T, seed = cfg["streams"], cfg["iterations"], cfg["seed"]
+    host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
+    g = rng.Generator(n, seed, device_buffer_bytes=cfg["device_buffer_bytes"])
+    g.profile_reset()
+    g.generate_to_host(T, host)
+    prof = g.profile()
+    cnt_k, _ = g.profile_stat("RNG_KERNEL")
+    cnt_r, _ = g.profile_stat("READ_BUFFER")
+    g.close()
+    out = host.numpy()
+    wx, ws, samples = oracle.row_checksums(n, seed, T, sample_every=16)
+    for j, i in enumerate(range(0, T, 16)):
+        assert np.array_equal(out[i], samples[j]), f"row {i} differs"
+    for i0 in range(0, T, 64):
+        x, s = _row_checksums(out[i0:i0 + 64])
+        assert np.array_equal(x, wx[i0:i0 + 64]), f"xor checksum differs in rows {i0}..{i0 + 63}"
+        assert np.array_equal(s, ws[i0:i0 + 64]), f"sum checksum differs in rows {i0}..{i0 + 63}"
+    # One row per 32 MiB buffer: one kernel and one read per iteration, and
+    # generation overlaps the reads.
+    assert cnt_k == T and cnt_r == T
+    assert prof["overlaps"], "no kernel/transfer overlap recorded"
+    assert prof["aggregate"]["READ_BUFFER"][0] > prof["aggregate"]["RNG_KERNEL"][0]
+
+
+def test_device_resident_full_size_sampled():
+    # Same workload kept on the device (the benchmark's device leg): sampled
+    # values one by one, plus the XOR checksum closed form on every row.
+    cfg = workloads.STREAMING
+    n, T, seed = cfg["streams"], cfg["iterations"], cfg["seed"]
+    g = rng.Generator(n, seed)
+    out = g.generate(T)
+    g.sync()
+    rs = np.random.default_rng(1)
+    rows = [0, 1, 2, 511, 1023] + list(rs.integers(0, T, 8))
+    cols = list(rs.integers(0, n, 64)) + [0, 1, n - 2, n - 1]
+    o64 = out.view(torch.int64)
+    sub = o64[torch.tensor(rows, device="cuda")][:, torch.tensor(cols, device="cuda")].cpu().numpy().view(np.uint64)
+    for a, i in enumerate(rows):
+        for b, gg in enumerate(cols):
+            assert int(sub[a, b]) == oracle.value(int(gg), seed, int(i)), (i, gg)
+    # Whole-row checksums of a few rows against the oracle's.
+    wx, ws, _ = oracle.row_checksums(n, seed, 4)
+    x, s = _row_checksums(out[:4].cpu().numpy())
+    assert np.array_equal(x, wx) and np.array_equal(s, ws)
+    del out
+    g.close()
