@@ -32,7 +32,10 @@ class Batch:
         lib.rng_batch_opts_default(ctypes.byref(o))
         o.values_per_thread = values_per_thread
         o.tune_reps = tune_reps
-        o.stream = None if stream is None else (stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream))
+        if stream is None:
+            stream = torch.cuda.Stream(device=self.device)  # pooled by torch, never destroyed
+        self._torch_stream = stream
+        o.stream = stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
         o.device = -1 if device is None else device
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -48,7 +51,9 @@ class Batch:
         C.check(self._lib.rng_batch_sync, self._h)
 
     @property
-    def stream(self) -> torch.cuda.ExternalStream:
+    def stream(self):
+        if isinstance(self._torch_stream, torch.cuda.Stream):
+            return self._torch_stream
         return torch.cuda.ExternalStream(self._lib.rng_batch_stream(self._h), device=self.device)
 
     def config(self):

@@ -25,6 +25,8 @@
 #include "prng_math.cuh"
 
 namespace rngi {
+rng_prof *prof_create_owned();
+void prof_destroy_owned(rng_prof *p);
 void prof_clear(rng_prof *p);
 void prof_add(rng_prof *p, const char *queue, const char *name, double s, double e);
 }  // namespace rngi
@@ -447,7 +449,7 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   if (!rc) rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&g->copy, cudaStreamNonBlocking), "cudaStreamCreate");
   if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&g->d_state, streams * 8), "cudaMalloc(state)");
   if (!rc) rc = profile_restart(g, err);
-  if (!rc) g->prof = rng_prof_new();
+  if (!rc) g->prof = rngi::prof_create_owned();
   if (!rc && !g->prof) rc = rngi::fail(err, RNG_ENOMEM, "rng_create: profiler allocation failed");
   if (rc) {
     rng_destroy(g);
@@ -474,7 +476,7 @@ void rng_destroy(rng_gen *g) {
   if (g->origin) cudaEventDestroy(g->origin);
   if (g->copy) cudaStreamDestroy(g->copy);
   if (g->own_compute && g->compute) cudaStreamDestroy(g->compute);
-  rng_prof_destroy(g->prof);
+  rngi::prof_destroy_owned(g->prof);
   delete g;
   rngi::live_dec();
 }

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <map>
 #include <string>
 #include <utility>
@@ -42,6 +43,10 @@ struct rng_prof {
 };
 
 namespace rngi {
+// Profilers owned by a generator are not separate library objects: they are
+// created and destroyed with it and are not counted by rng_live_objects().
+rng_prof *prof_create_owned() { return new (std::nothrow) rng_prof(); }
+void prof_destroy_owned(rng_prof *p) { delete p; }
 void prof_clear(rng_prof *p) {
   p->events.clear();
   p->calculated = false;

@@ -45,14 +45,18 @@ class Generator:
         o.device_buffer_bytes = device_buffer_bytes
         o.host_slots = host_slots
         o.profiling = 1 if profiling else 0
-        h = _stream_handle(compute_stream)
-        o.compute_stream = h
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        if compute_stream is None:
+            # A stream from torch's pool: it outlives this object, so tensors
+            # that recorded it stay safe to free after close().
+            compute_stream = torch.cuda.Stream(device=self.device)
+        self._torch_stream = compute_stream
+        o.compute_stream = _stream_handle(compute_stream)
         o.device = -1 if device is None else device
         o.store_policy = store_policy
         o.host_wait_ms = host_wait_ms
         self._lib = lib
         self._h = ctypes.c_void_p()
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             C.check(lib.rng_create, streams, seed & ((1 << 64) - 1), ctypes.byref(o), ctypes.byref(self._h))
         self.streams = streams
@@ -89,7 +93,10 @@ class Generator:
         return p.value
 
     @property
-    def stream(self) -> torch.cuda.ExternalStream:
+    def stream(self):
+        """The compute stream the library launches on."""
+        if isinstance(self._torch_stream, torch.cuda.Stream):
+            return self._torch_stream
         return torch.cuda.ExternalStream(self._lib.rng_compute_stream(self._h), device=self.device)
 
     def launch_config(self):
