@@ -280,7 +280,7 @@ def run_gpu(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl["name"], "streams_per_gpu": n, "iterations": T, "seed": seed,
                    "bytes_per_step_per_gpu": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
-                   "l2": "output 32 GiB per step > 129 MB L2: no flush needed",
+                   "l2": f"output {nbytes / GIB:g} GiB per step > 129 MB L2: no flush needed",
                    "parallelism": f"dp{ws} (disjoint stream-id blocks)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -314,9 +314,14 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=128, help="iterations in the CPU-baseline sample")
     ap.add_argument("--reference-rows", type=int, default=16, help="iterations per reference step")
+    ap.add_argument("--iterations", type=int, default=0,
+                    help="override the workload's iteration count (profiling captures of a smaller case)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.iterations:
+        wl["iterations"] = args.iterations
+        wl["name"] = re.sub(r"x \d+ iterations", f"x {args.iterations} iterations", wl["name"])
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

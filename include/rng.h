@@ -72,8 +72,11 @@ uint64_t rng_launch_count(void);
 /* ------------------------------------------------------------------ */
 typedef struct rng_opts {
     uint32_t struct_size;         /* sizeof(rng_opts), set by rng_opts_default */
-    uint32_t values_per_thread;   /* streams per GPU thread: 1,2,4,...,64; 0 = choose */
-    uint32_t block_threads;       /* threads per block: 128, 256 or 512; 0 = 256 */
+    uint32_t values_per_thread;   /* streams per GPU thread: 1-8, 10, 12, 14, 16, 20,
+                                     24, 28, 32, 48 or 64; 0 = choose */
+    uint32_t block_threads;       /* threads per block: 256 (0 = 256), or 128, 512,
+                                     1024 with values_per_thread 2, 4, 6, 8, 12,
+                                     16 or 24 (one 8-byte streaming store per value) */
     uint32_t fuse_init;           /* 1 (default): rng_init launches nothing and the
                                      first rng_generate hashes the ids itself;
                                      0: rng_init runs the separate init kernel */
@@ -90,6 +93,10 @@ typedef struct rng_opts {
     uint32_t store_policy;        /* 0 = default stores, 1 = streaming (.cs) */
     uint32_t host_wait_ms;        /* longest wait for a free staging slot while a
                                      host consumer holds them all; 0 = 600000 */
+    uint32_t store_width;         /* values per store instruction: 1, 2 or 4;
+                                     0 = the widest the output's alignment allows */
+    uint32_t grid_blocks;         /* cap on the persistent grid; 0 = every block
+                                     that can be resident */
 } rng_opts;
 
 void rng_opts_default(rng_opts *opts);
@@ -269,6 +276,66 @@ int rng_batch_config(const rng_batch *b, uint32_t *values_per_thread,
                      uint64_t *work_units, double *tuned_ms);
 void *rng_batch_stream(rng_batch *b);
 void rng_batch_destroy(rng_batch *b);
+
+/* ------------------------------------------------------------------ */
+/* Served form: continuous batching of generation requests             */
+/* ------------------------------------------------------------------ */
+/* A request asks for iterations 0 .. iterations-1 (iteration-major, the
+ * layout of Section 5) of a generator with `streams` streams and run seed
+ * `seed`.  A scheduler thread admits queued requests in arrival order while
+ * the device-memory budget (outputs plus states) and the slot count allow,
+ * and launches steps: one work-list kernel per step covering the next rows
+ * of every admitted request, so requests that arrive while others run join
+ * the next step.  Requests larger than one step's quantum continue over
+ * several steps from their device-resident states.  Every result is
+ * identical to the same request served alone. */
+typedef struct rng_server rng_server;
+
+typedef struct rng_server_opts {
+    uint32_t struct_size;
+    uint32_t max_active;          /* requests admitted at once; default 1024 */
+    uint64_t hbm_budget_bytes;    /* device arena for outputs and states; default 64 GiB */
+    uint64_t step_bytes;          /* output bytes one step aims to produce; default 512 MiB */
+    uint32_t max_steps_in_flight; /* launched, unfinished steps; default 2 */
+    uint32_t values_per_thread;   /* 1..32 (power of two); 0 = 8 */
+    uint32_t max_units_per_step;  /* work-table capacity per step; default 1<<20 */
+    int32_t device;               /* -1 = current */
+    void *stream;                 /* cudaStream_t; NULL = own stream */
+} rng_server_opts;
+
+typedef struct rng_server_stats {
+    uint64_t submitted, completed, rejected, released;
+    uint64_t steps, bytes_generated;
+    uint64_t pending, active, bytes_in_use, peak_bytes_in_use, peak_active;
+} rng_server_stats;
+
+void rng_server_opts_default(rng_server_opts *opts);
+/* Allocates the arena (one device allocation of hbm_budget_bytes) and
+ * starts the scheduler thread. */
+int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **err);
+/* Queues a request; non-blocking.  *ticket identifies it (>= 1).
+ * RNG_EBUDGET if 8*streams*(iterations+1) bytes exceed the whole budget,
+ * RNG_EINVAL for sizes out of range (1 <= streams <= 2^32, iterations >= 1),
+ * or the scheduler's error if it has failed. */
+int rng_server_submit(rng_server *s, uint64_t seed, uint64_t streams, uint64_t iterations,
+                      uint64_t *ticket, rng_err **err);
+/* Returns up to `max` completed requests not returned before: ticket,
+ * device address of its output (8*streams*iterations bytes, owned by the
+ * server until released) and latency in seconds (submission to completion
+ * seen by the scheduler).  Waits up to timeout_ms for the first one;
+ * *n_done = 0 on timeout. */
+int rng_server_poll(rng_server *s, uint32_t max, uint64_t *tickets, uint64_t **outs,
+                    double *latency_s, uint32_t *n_done, uint32_t timeout_ms, rng_err **err);
+/* Copies `count` values starting at value `first` of a completed request's
+ * output to host memory (blocking). */
+int rng_server_read(rng_server *s, uint64_t ticket, uint64_t first, uint64_t count,
+                    uint64_t *host_dst, rng_err **err);
+/* Returns a completed request's output memory to the budget. */
+int rng_server_release(rng_server *s, uint64_t ticket, rng_err **err);
+int rng_server_get_stats(rng_server *s, rng_server_stats *stats);
+/* Finishes the steps in flight, drops queued requests, frees the arena.
+ * NULL-safe. */
+void rng_server_destroy(rng_server *s);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@ from ._capi import RngError, load, library_path  # noqa: F401
 from .builder import build  # noqa: F401
 from .generator import Generator, Profiler  # noqa: F401
 from .batch import Batch  # noqa: F401
+from .serve import Server, run_load  # noqa: F401
 
 
 def launch_count() -> int:

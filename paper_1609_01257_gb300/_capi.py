@@ -42,6 +42,8 @@ class RngOpts(ctypes.Structure):
         ("device", c_i32),
         ("store_policy", c_u32),
         ("host_wait_ms", c_u32),
+        ("store_width", c_u32),
+        ("grid_blocks", c_u32),
     ]
 
 
@@ -54,6 +56,26 @@ class RngBatchOpts(ctypes.Structure):
         ("stream", c_vp),
         ("device", c_i32),
     ]
+
+
+class RngServerOpts(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", c_u32),
+        ("max_active", c_u32),
+        ("hbm_budget_bytes", c_u64),
+        ("step_bytes", c_u64),
+        ("max_steps_in_flight", c_u32),
+        ("values_per_thread", c_u32),
+        ("max_units_per_step", c_u32),
+        ("device", c_i32),
+        ("stream", c_vp),
+    ]
+
+
+class RngServerStats(ctypes.Structure):
+    _fields_ = [(n, c_u64) for n in (
+        "submitted", "completed", "rejected", "released", "steps", "bytes_generated",
+        "pending", "active", "bytes_in_use", "peak_bytes_in_use", "peak_active")]
 
 
 P_err = ctypes.POINTER(ctypes.POINTER(RngErr))
@@ -109,6 +131,15 @@ SIGNATURES = {
                           P_u64, ctypes.POINTER(c_dbl)], c_int),
     "rng_batch_stream": ([c_vp], c_vp),
     "rng_batch_destroy": ([c_vp], None),
+    "rng_server_opts_default": ([ctypes.POINTER(RngServerOpts)], None),
+    "rng_server_create": ([ctypes.POINTER(RngServerOpts), ctypes.POINTER(c_vp), P_err], c_int),
+    "rng_server_submit": ([c_vp, c_u64, c_u64, c_u64, P_u64, P_err], c_int),
+    "rng_server_poll": ([c_vp, c_u32, P_u64, ctypes.POINTER(c_vp), ctypes.POINTER(c_dbl),
+                         ctypes.POINTER(c_u32), c_u32, P_err], c_int),
+    "rng_server_read": ([c_vp, c_u64, c_u64, c_u64, c_vp, P_err], c_int),
+    "rng_server_release": ([c_vp, c_u64, P_err], c_int),
+    "rng_server_get_stats": ([c_vp, ctypes.POINTER(RngServerStats)], c_int),
+    "rng_server_destroy": ([c_vp], None),
 }
 
 

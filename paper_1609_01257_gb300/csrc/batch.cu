@@ -153,10 +153,13 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
   for (uint32_t k = 0; k < count; ++k) {
     rngi::BatchInstance in;
     in.out = outs[k];
+    in.state = nullptr;
     in.streams = streams[k];
     in.rows = iterations[k];
     in.key = prng::seed_key(seeds[k]);
     in.vec = (streams[k] % 2 == 0) && (reinterpret_cast<uintptr_t>(outs[k]) % 16 == 0);
+    in.from_hash = 1;
+    in.write_state = 0;
     b->inst.push_back(in);
   }
   int rc = RNG_OK;

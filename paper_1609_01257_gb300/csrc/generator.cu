@@ -75,8 +75,6 @@ struct rng_gen {
 
 namespace {
 
-bool is_pow2_upto(uint32_t v, uint32_t cap) { return v && v <= cap && (v & (v - 1)) == 0; }
-
 cudaError_t next_event(rng_gen *g, size_t *idx) {
   if (g->ev_used == g->evpool.size()) {
     cudaEvent_t e;
@@ -185,12 +183,13 @@ int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_
   a.from_hash = from_hash;
   a.write_state = 1;
   if (c.span != g->chunk_span) {
-    g->chunk_shape = rngi::rows_shape(c.span, g->opts.values_per_thread, g->opts.block_threads, g->device);
+    g->chunk_shape = rngi::rows_shape(c.span, g->opts.values_per_thread, g->opts.block_threads, g->device,
+                                      g->opts.grid_blocks);
     g->chunk_span = c.span;
   }
   const rngi::LaunchShape sh = g->chunk_shape;
   long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute);
+  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), static_cast<int>(g->opts.store_width), g->compute);
   op_end(g, op, g->compute);
   return rngi::cuda_fail(err, st, "rows kernel launch");
 }
@@ -409,14 +408,19 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
                         sizeof(rng_opts));
     o = *opts;
   }
-  if (o.values_per_thread && !is_pow2_upto(o.values_per_thread, 64))
-    return rngi::fail(err, RNG_EINVAL, "rng_create: values_per_thread must be 0 or a power of two <= 64");
-  if (o.block_threads && o.block_threads != 256)
-    return rngi::fail(err, RNG_EINVAL, "rng_create: block_threads must be 0 or 256");
+  if (o.values_per_thread && !rngi::rows_vpt_supported(o.values_per_thread))
+    return rngi::fail(err, RNG_EINVAL,
+                      "rng_create: values_per_thread must be 0 or one of 1-8, 10, 12, 14, 16, 20, 24, 28, 32, 48, 64");
+  if (o.block_threads && !rngi::rows_shape_supported(o.values_per_thread, o.block_threads))
+    return rngi::fail(err, RNG_EINVAL,
+                      "rng_create: block_threads must be 0 or 256, or 128/512/1024 with values_per_thread "
+                      "2, 4, 6, 8, 12, 16 or 24");
   if (o.device_buffer_bytes == 0) o.device_buffer_bytes = size_t(32) << 20;
   if (o.device_buffer_bytes < 16 || o.device_buffer_bytes % 16)
     return rngi::fail(err, RNG_EINVAL, "rng_create: device_buffer_bytes must be a positive multiple of 16");
   if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
+  if (o.store_width != 0 && o.store_width != 1 && o.store_width != 2 && o.store_width != 4)
+    return rngi::fail(err, RNG_EINVAL, "rng_create: store_width must be 0, 1, 2 or 4");
   if (o.stream_offset > (uint64_t(1) << 32) - streams)
     return rngi::fail(err, RNG_EINVAL, "rng_create: stream_offset + streams must not exceed 2^32");
 
@@ -437,7 +441,7 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   g->device = dev;
   g->opts = o;
   g->buf_bytes = o.device_buffer_bytes;
-  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev);
+  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev, o.grid_blocks);
   rngi::live_inc();
   int rc = RNG_OK;
   if (o.compute_stream) {
@@ -522,7 +526,7 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   a.from_hash = !g->materialized;
   a.write_state = 1;
   long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
+  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), static_cast<int>(g->opts.store_width), g->compute);
   op_end(g, op, g->compute);
   rc = rngi::cuda_fail(err, st, "rows kernel launch");
   if (rc) return rc;

@@ -41,9 +41,16 @@ struct LaunchShape {
   uint32_t grid;
 };
 
-// Picks values-per-thread (if vpt == 0), block size and a persistent grid.
-LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device);
-cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy,
+// Values-per-thread counts the row kernel is compiled for (256-thread
+// blocks), and the (values-per-thread, block) pairs of the other block sizes.
+bool rows_vpt_supported(uint32_t vpt);
+bool rows_shape_supported(uint32_t vpt, uint32_t block);
+// Picks values-per-thread (if vpt == 0), block size and a persistent grid of
+// at most max_grid blocks (0: as many as can be resident).
+LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid = 0);
+// store_policy: 0 default, 1 streaming (.cs); max_width: widest store in
+// values (1, 2, 4), 0 = widest the alignment allows.
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, int max_width,
                         cudaStream_t st);
 cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
                         cudaStream_t st);
@@ -51,13 +58,20 @@ cudaError_t launch_checksum(const RowsLaunch &a, const LaunchShape &sh, uint64_t
                             uint64_t *row_sum, cudaStream_t st);
 int device_sm_count(int device);
 
-// Batched kernel tables.
+// Work-list kernel tables (batched and served forms).  One entry is a chunk
+// of consecutive iterations of one generator instance: rows `rows` of its
+// output starting at `out` (row pitch = streams).  Its streams start from the
+// id hash (from_hash) or from `state`, and end states are stored back to
+// `state` when write_state is set.
 struct BatchInstance {
   uint64_t *out;
+  uint64_t *state;
   uint64_t streams;
   uint64_t rows;
   uint32_t key;
-  uint32_t vec;     // 1: rows are 16-byte aligned (vector stores allowed)
+  uint32_t vec;         // 1: rows are 16-byte aligned (vector stores allowed)
+  uint32_t from_hash;
+  uint32_t write_state;
 };
 struct BatchUnit {
   uint32_t inst;

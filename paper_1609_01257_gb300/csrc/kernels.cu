@@ -35,34 +35,54 @@ __device__ __forceinline__ void store_one(uint64_t *p, uint64_t a) {
     asm volatile("st.global.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
 }
 
+// 32-byte store (256-bit vector stores exist for global memory on sm_100+).
+template <int POLICY>
+__device__ __forceinline__ void store_quad(uint64_t *p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+  if (POLICY == kPolicyStreaming)
+    asm volatile("st.global.cs.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
+                 : "memory");
+  else
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
+                 : "memory");
+}
+
+// W consecutive values with one store (W = 1, 2 or 4; p aligned to 8*W bytes).
+template <int W, int POLICY>
+__device__ __forceinline__ void store_vec(uint64_t *p, const uint64_t *v) {
+  if (W == 4)
+    store_quad<POLICY>(p, v[0], v[1], v[2], v[3]);
+  else if (W == 2)
+    store_pair<POLICY>(p, v[0], v[1]);
+  else
+    store_one<POLICY>(p, v[0]);
+}
+
 // Stream offset (within a tile) of value q of store slot j for thread t:
 // slot j of all threads of the block forms one contiguous run of
 // blockDim * P values, so every warp-wide store is 32 * 8 * P contiguous bytes.
 constexpr int kBlock = 256;  // threads per block of every generation kernel
 
-template <int P>
+template <int P, int BLOCK>
 __device__ __forceinline__ uint64_t slot_offset(int j, int q) {
-  return static_cast<uint64_t>(P) * (threadIdx.x + static_cast<uint64_t>(kBlock) * j) + q;
+  return static_cast<uint64_t>(P) * (threadIdx.x + static_cast<uint64_t>(BLOCK) * j) + q;
 }
 
-// Emits `rows` rows of one tile.  CHECK: some values of the tile lie past
-// the end of the stream range and must not be stored.
-template <int VPT, bool VEC, int POLICY, bool CHECK>
+// Emits `rows` rows of one tile, W values per store.  CHECK: some values of
+// the tile lie past the end of the stream range and must not be stored.
+template <int VPT, int W, int POLICY, bool CHECK, int BLOCK = kBlock>
 __device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, uint64_t pitch,
                                           uint64_t rows, uint64_t rel0, uint64_t span) {
-  constexpr int P = VEC ? 2 : 1;
-  constexpr int J = VPT / P;
+  constexpr int J = VPT / W;
   for (uint64_t r = 0; r < rows; ++r, row += pitch) {
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      const uint64_t rel = rel0 + slot_offset<P>(j, 0);
-      if (VEC) {
-        if (!CHECK || rel + 1 < span)
-          store_pair<POLICY>(row + rel, st[2 * j], st[2 * j + 1]);
-        else if (rel < span)
-          store_one<POLICY>(row + rel, st[2 * j]);
+      const uint64_t rel = rel0 + slot_offset<W, BLOCK>(j, 0);
+      if (!CHECK || rel + W <= span) {
+        store_vec<W, POLICY>(row + rel, &st[W * j]);
       } else {
-        if (!CHECK || rel < span) store_one<POLICY>(row + rel, st[j]);
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+          if (rel + q < span) store_one<POLICY>(row + rel + q, st[W * j + q]);
       }
     }
 #pragma unroll
@@ -70,15 +90,14 @@ __device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, ui
   }
 }
 
-template <int VPT, bool VEC>
+template <int VPT, int P, int BLOCK = kBlock>
 __device__ __forceinline__ void load_tile(uint64_t (&st)[VPT], const RowsLaunch &a, uint64_t rel0,
                                           uint64_t span) {
-  constexpr int P = VEC ? 2 : 1;
 #pragma unroll
   for (int j = 0; j < VPT / P; ++j)
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      const uint64_t rel = rel0 + slot_offset<P>(j, q);
+      const uint64_t rel = rel0 + slot_offset<P, BLOCK>(j, q);
       const uint64_t s = a.s_begin + rel;
       uint64_t v = 0;
       if (rel < span) v = a.from_hash ? prng::initial_state(a.id_base + s, a.key) : a.state[s];
@@ -86,41 +105,40 @@ __device__ __forceinline__ void load_tile(uint64_t (&st)[VPT], const RowsLaunch 
     }
 }
 
-template <int VPT, bool VEC>
+template <int VPT, int P, int BLOCK = kBlock>
 __device__ __forceinline__ void store_tile_state(const uint64_t (&st)[VPT], const RowsLaunch &a,
                                                  uint64_t rel0, uint64_t span) {
-  constexpr int P = VEC ? 2 : 1;
 #pragma unroll
   for (int j = 0; j < VPT / P; ++j)
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      const uint64_t rel = rel0 + slot_offset<P>(j, q);
+      const uint64_t rel = rel0 + slot_offset<P, BLOCK>(j, q);
       if (rel < span) a.state[a.s_begin + rel] = st[j * P + q];
     }
 }
 
 // Persistent row kernel: blocks walk the tiles of blockDim * VPT streams;
 // each thread holds VPT states in registers across all rows of its tile.
-template <int VPT, bool VEC, int POLICY>
-__global__ void __launch_bounds__(kBlock) rows_kernel(const RowsLaunch a) {
+template <int VPT, int W, int POLICY, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
   const uint64_t span = a.s_end - a.s_begin;
-  const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  const uint64_t tile_vals = static_cast<uint64_t>(BLOCK) * VPT;
   const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
   for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const uint64_t rel0 = tile * tile_vals;
     uint64_t st[VPT];
-    load_tile<VPT, VEC>(st, a, rel0, span);
+    load_tile<VPT, W, BLOCK>(st, a, rel0, span);
     if (a.out) {
       if (rel0 + tile_vals <= span)
-        emit_rows<VPT, VEC, POLICY, false>(st, a.out, a.pitch, a.rows, rel0, span);
+        emit_rows<VPT, W, POLICY, false, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span);
       else
-        emit_rows<VPT, VEC, POLICY, true>(st, a.out, a.pitch, a.rows, rel0, span);
+        emit_rows<VPT, W, POLICY, true, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span);
     } else {
       for (uint64_t r = 0; r < a.rows; ++r)
 #pragma unroll
         for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
     }
-    if (a.write_state) store_tile_state<VPT, VEC>(st, a, rel0, span);
+    if (a.write_state) store_tile_state<VPT, W, BLOCK>(st, a, rel0, span);
   }
 }
 
@@ -163,7 +181,7 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
   for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const uint64_t rel0 = tile * tile_vals;
     uint64_t st[VPT];
-    load_tile<VPT, false>(st, a, rel0, span);
+    load_tile<VPT, 1>(st, a, rel0, span);
     for (uint64_t r = 0; r < a.rows; ++r) {
       uint64_t x = 0, s = 0;
 #pragma unroll
@@ -191,18 +209,18 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
     }
     // Values past the end of the range were loaded as 0 and advance to 0,
     // so they add nothing; the states of real streams are written back.
-    if (a.write_state) store_tile_state<VPT, false>(st, a, rel0, span);
+    if (a.write_state) store_tile_state<VPT, 1>(st, a, rel0, span);
     __syncthreads();
   }
 }
 
-// Batched persistent kernel: blocks take work units (instance, tile of
-// streams) from a shared counter, largest units first, and emit all rows of
-// the unit from the hash of the ids (every instance starts at iteration 0).
+// Work-list persistent kernel (batched and served forms): blocks take work
+// units (one tile of streams of one chunk) from a shared counter -- the
+// table lists the largest units first -- and emit all rows of the unit.
 template <int VPT>
-__global__ void __launch_bounds__(kBlock) batch_kernel(const BatchInstance *__restrict__ inst,
-                                                    const BatchUnit *__restrict__ units,
-                                                    uint32_t n_units, uint32_t *counter) {
+__global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *__restrict__ inst,
+                                                          const BatchUnit *__restrict__ units,
+                                                          uint32_t n_units, uint32_t *counter) {
   __shared__ uint32_t s_unit;
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
@@ -213,7 +231,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchInstance *__re
     const BatchUnit wu = units[u];
     const BatchInstance in = inst[wu.inst];
     RowsLaunch a;
-    a.state = nullptr;
+    a.state = in.state;
     a.out = in.out;
     a.pitch = in.streams;
     a.s_begin = wu.s_begin;
@@ -221,56 +239,83 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchInstance *__re
     a.id_base = 0;
     a.rows = in.rows;
     a.key = in.key;
-    a.from_hash = 1;
-    a.write_state = 0;
+    a.from_hash = in.from_hash;
+    a.write_state = in.write_state;
     const uint64_t span = wu.count;
     const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
     uint64_t *row = in.out + wu.s_begin;
-    if (in.vec && (VPT % 2 == 0)) {
+    if (VPT % 2 == 0 && in.vec) {
       constexpr int V2 = VPT >= 2 ? VPT : 2;
       uint64_t st[V2];
-      load_tile<V2, true>(reinterpret_cast<uint64_t(&)[V2]>(st), a, 0, span);
+      load_tile<V2, 2>(st, a, 0, span);
       if (span == tile_vals)
-        emit_rows<V2, true, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<V2, 2, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
       else
-        emit_rows<V2, true, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<V2, 2, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+      if (a.write_state) store_tile_state<V2, 2>(st, a, 0, span);
     } else {
       uint64_t st[VPT];
-      load_tile<VPT, false>(st, a, 0, span);
+      load_tile<VPT, 1>(st, a, 0, span);
       if (span == tile_vals)
-        emit_rows<VPT, false, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<VPT, 1, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
       else
-        emit_rows<VPT, false, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<VPT, 1, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+      if (a.write_state) store_tile_state<VPT, 1>(st, a, 0, span);
     }
   }
 }
 
-template <int VPT, bool VEC, int POLICY>
-const void *rows_fn() {
-  return reinterpret_cast<const void *>(&rows_kernel<VPT, VEC, POLICY>);
+template <int VPT, int W>
+const void *rows_fn_policy(int policy) {
+  return policy == kPolicyStreaming
+             ? reinterpret_cast<const void *>(&rows_kernel<VPT, W, kPolicyStreaming, kBlock>)
+             : reinterpret_cast<const void *>(&rows_kernel<VPT, W, kPolicyDefault, kBlock>);
 }
 
-template <int VPT>
-const void *rows_fn_dispatch(bool vec, int policy) {
-  if (VPT >= 2 && vec) {
-    constexpr int V = VPT >= 2 ? VPT : 2;
-    return policy == kPolicyStreaming ? rows_fn<V, true, kPolicyStreaming>()
-                                      : rows_fn<V, true, kPolicyDefault>();
-  }
-  return policy == kPolicyStreaming ? rows_fn<VPT, false, kPolicyStreaming>()
-                                    : rows_fn<VPT, false, kPolicyDefault>();
-}
-
-const void *select_rows(uint32_t vpt, bool vec, int policy) {
+// Larger blocks (one store per value, streaming policy): wider contiguous
+// runs per block and row with the same registers per thread.
+template <int BLOCK>
+const void *rows_fn_wide(uint32_t vpt) {
   switch (vpt) {
-    case 1: return rows_fn_dispatch<1>(false, policy);
-    case 2: return rows_fn_dispatch<2>(vec, policy);
-    case 4: return rows_fn_dispatch<4>(vec, policy);
-    case 8: return rows_fn_dispatch<8>(vec, policy);
-    case 16: return rows_fn_dispatch<16>(vec, policy);
-    case 32: return rows_fn_dispatch<32>(vec, policy);
-    case 64: return rows_fn_dispatch<64>(vec, policy);
+    case 2: return reinterpret_cast<const void *>(&rows_kernel<2, 1, kPolicyStreaming, BLOCK>);
+    case 4: return reinterpret_cast<const void *>(&rows_kernel<4, 1, kPolicyStreaming, BLOCK>);
+    case 6: return reinterpret_cast<const void *>(&rows_kernel<6, 1, kPolicyStreaming, BLOCK>);
+    case 8: return reinterpret_cast<const void *>(&rows_kernel<8, 1, kPolicyStreaming, BLOCK>);
+    case 12: return reinterpret_cast<const void *>(&rows_kernel<12, 1, kPolicyStreaming, BLOCK>);
+    case 16: return reinterpret_cast<const void *>(&rows_kernel<16, 1, kPolicyStreaming, BLOCK>);
+    case 24: return reinterpret_cast<const void *>(&rows_kernel<24, 1, kPolicyStreaming, BLOCK>);
     default: return nullptr;
+  }
+}
+
+// Widest store width W <= width that divides VPT (W in {1, 2, 4}).
+template <int VPT>
+const void *rows_fn_dispatch(int width, int policy) {
+  if constexpr (VPT % 4 == 0) {
+    if (width >= 4) return rows_fn_policy<VPT, 4>(policy);
+  }
+  if constexpr (VPT % 2 == 0) {
+    if (width >= 2) return rows_fn_policy<VPT, 2>(policy);
+  }
+  return rows_fn_policy<VPT, 1>(policy);
+}
+
+#define RNG_FOR_EACH_VPT(X) \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14) X(16) X(20) X(24) X(28) X(32) X(48) X(64)
+
+const void *select_rows(uint32_t vpt, int width, int policy, uint32_t block = kBlock) {
+  if (block == 512) return rows_fn_wide<512>(vpt);
+  if (block == 1024) return rows_fn_wide<1024>(vpt);
+  if (block == 128) return rows_fn_wide<128>(vpt);
+  if (block != kBlock) return nullptr;
+  switch (vpt) {
+#define RNG_CASE(V) \
+  case V:           \
+    return rows_fn_dispatch<V>(width, policy);
+    RNG_FOR_EACH_VPT(RNG_CASE)
+#undef RNG_CASE
+    default:
+      return nullptr;
   }
 }
 
@@ -289,12 +334,12 @@ const void *select_checksum(uint32_t vpt) {
 
 const void *select_batch(uint32_t vpt) {
   switch (vpt) {
-    case 1: return reinterpret_cast<const void *>(&batch_kernel<1>);
-    case 2: return reinterpret_cast<const void *>(&batch_kernel<2>);
-    case 4: return reinterpret_cast<const void *>(&batch_kernel<4>);
-    case 8: return reinterpret_cast<const void *>(&batch_kernel<8>);
-    case 16: return reinterpret_cast<const void *>(&batch_kernel<16>);
-    case 32: return reinterpret_cast<const void *>(&batch_kernel<32>);
+    case 1: return reinterpret_cast<const void *>(&worklist_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&worklist_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&worklist_kernel<4>);
+    case 8: return reinterpret_cast<const void *>(&worklist_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&worklist_kernel<16>);
+    case 32: return reinterpret_cast<const void *>(&worklist_kernel<32>);
     default: return nullptr;
   }
 }
@@ -317,10 +362,9 @@ int device_sm_count(int device) {
   return sms;
 }
 
-LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device) {
+LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid) {
   LaunchShape sh;
-  (void)block;
-  sh.block = kBlock;
+  sh.block = block ? block : kBlock;
   const int sms = device_sm_count(device);
   if (vpt == 0) {
     // Largest values-per-thread (<= 16) that still gives every SM at least
@@ -334,21 +378,34 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
       }
   }
   sh.vpt = vpt;
-  const void *fn = select_rows(vpt, vpt >= 2, kPolicyDefault);
+  const void *fn = select_rows(vpt, sh.block == kBlock ? 4 : 1, sh.block == kBlock ? kPolicyDefault : kPolicyStreaming, sh.block);
+  if (!fn) {
+    sh.grid = 0;
+    return sh;
+  }
   const uint64_t tiles = (streams + static_cast<uint64_t>(sh.block) * vpt - 1) /
                          (static_cast<uint64_t>(sh.block) * vpt);
   const uint64_t resident = static_cast<uint64_t>(sms) * occupancy(fn, sh.block);
   uint64_t grid = tiles < resident ? tiles : resident;
+  if (max_grid && grid > max_grid) grid = max_grid;
   sh.grid = static_cast<uint32_t>(grid ? grid : 1);
   return sh;
 }
 
-cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy,
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, int max_width,
                         cudaStream_t st) {
-  const bool vec = sh.vpt >= 2 && a.out && (a.pitch % 2 == 0) &&
-                   (reinterpret_cast<uintptr_t>(a.out) % 16 == 0);
-  const void *fn = select_rows(sh.vpt, vec, store_policy);
-  if (!fn || sh.block != kBlock) return cudaErrorInvalidValue;
+  // Widest store the output's alignment allows: every row must start on an
+  // 8*W-byte boundary (pitch a multiple of W, base aligned to 8*W bytes).
+  int width = 1;
+  const uintptr_t base = reinterpret_cast<uintptr_t>(a.out);
+  for (int w : {4, 2})
+    if (a.out && a.pitch % w == 0 && base % (8 * w) == 0) {
+      width = w;
+      break;
+    }
+  if (max_width > 0 && width > max_width) width = max_width;
+  const void *fn = select_rows(sh.vpt, width, store_policy, sh.block);
+  if (!fn) return cudaErrorInvalidValue;
   RowsLaunch args = a;
   void *params[] = {&args};
   cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
@@ -380,6 +437,11 @@ cudaError_t launch_checksum(const RowsLaunch &a, const LaunchShape &sh, uint64_t
   cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
   if (e == cudaSuccess) count_launch();
   return e;
+}
+
+bool rows_vpt_supported(uint32_t vpt) { return select_rows(vpt, 1, kPolicyDefault) != nullptr; }
+bool rows_shape_supported(uint32_t vpt, uint32_t block) {
+  return select_rows(vpt ? vpt : 8, 1, kPolicyStreaming, block ? block : kBlock) != nullptr;
 }
 
 int batch_blocks_per_sm(uint32_t vpt, uint32_t block) {

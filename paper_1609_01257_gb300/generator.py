@@ -35,7 +35,8 @@ class Generator:
                  fuse_init: bool = True, stream_offset: int = 0,
                  device_buffer_bytes: int = 32 << 20, host_slots: int = 2,
                  profiling: bool = True, compute_stream=None, device: Optional[int] = None,
-                 store_policy: int = 0, host_wait_ms: int = 0, init: bool = True):
+                 store_policy: int = 0, host_wait_ms: int = 0, store_width: int = 0,
+                 block_threads: int = 0, grid_blocks: int = 0, init: bool = True):
         lib = C.load()
         o = C.RngOpts()
         lib.rng_opts_default(ctypes.byref(o))
@@ -55,6 +56,9 @@ class Generator:
         o.device = -1 if device is None else device
         o.store_policy = store_policy
         o.host_wait_ms = host_wait_ms
+        o.store_width = store_width
+        o.block_threads = block_threads
+        o.grid_blocks = grid_blocks
         self._lib = lib
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -56,7 +56,7 @@ def test_bad_arguments_return_status_not_crash(L):
     assert rc == C.RNG_EINVAL
     o = C.RngOpts()
     L.rng_opts_default(ctypes.byref(o))
-    o.values_per_thread = 3
+    o.values_per_thread = 9  # not a compiled shape
     assert L.rng_create(16, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL
     o.values_per_thread = 0
     o.struct_size = 4

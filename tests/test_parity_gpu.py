@@ -37,11 +37,16 @@ def test_ragged_sizes(n, T):
     assert np.array_equal(got, oracle.generate(n, 12345, T))
 
 
-@pytest.mark.parametrize("vpt", [1, 2, 4, 8, 16, 32, 64])
-@pytest.mark.parametrize("n", [4096 * 3 + 2, 100_001])
+VPTS = [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 48, 64]
+
+
+@pytest.mark.parametrize("vpt", VPTS)
+@pytest.mark.parametrize("n", [4096 * 3 + 4, 100_001, 100_002])
 def test_values_per_thread_variants(vpt, n):
-    got = dev_gen(n, 99, 9, values_per_thread=vpt)
-    assert np.array_equal(got, oracle.generate(n, 99, 9))
+    want = oracle.generate(n, 99, 9)
+    for width in (1, 2, 4):
+        got = dev_gen(n, 99, 9, values_per_thread=vpt, store_width=width)
+        assert np.array_equal(got, want), (vpt, width)
 
 
 @pytest.mark.parametrize("policy", [0, 1])
