@@ -291,7 +291,7 @@ def run_gpu(args, wl):
         "clocks": clk,
     }
     if not args.skip_cpu_baseline and ws == 1:
-        rows = args.cpu_rows
+        rows = args.cpu_rows or T
         nb, dt = cpu_oracle_sample(n, seed, rows)
         line["cpu_baseline"] = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} streams x first {rows} iterations ({nb / GIB:.1f} GiB), "
@@ -312,7 +312,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=128, help="iterations in the CPU-baseline sample")
+    ap.add_argument("--cpu-rows", type=int, default=0,
+                    help="iterations in the CPU-baseline sample (0 = the whole workload)")
     ap.add_argument("--reference-rows", type=int, default=16, help="iterations per reference step")
     ap.add_argument("--iterations", type=int, default=0,
                     help="override the workload's iteration count (profiling captures of a smaller case)")

@@ -90,11 +90,14 @@ typedef struct rng_opts {
                                      CUDA events for the profiler */
     void *compute_stream;         /* cudaStream_t for kernels; NULL = own stream */
     int32_t device;               /* CUDA device ordinal; -1 = current device */
-    uint32_t store_policy;        /* 0 = default stores, 1 = streaming (.cs) */
+    uint32_t store_policy;        /* 0 = default stores, 1 (default) = streaming
+                                     stores (st.global.cs, evict-first) */
     uint32_t host_wait_ms;        /* longest wait for a free staging slot while a
                                      host consumer holds them all; 0 = 600000 */
-    uint32_t store_width;         /* values per store instruction: 1, 2 or 4;
-                                     0 = the widest the output's alignment allows */
+    uint32_t store_width;         /* widest store in values: 1, 2 or 4 (the
+                                     output's alignment may force narrower);
+                                     0 = per shape (1 for >= 6 values per
+                                     thread, else 4) */
     uint32_t grid_blocks;         /* cap on the persistent grid; 0 = every block
                                      that can be resident */
 } rng_opts;

@@ -184,12 +184,12 @@ int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_
   a.write_state = 1;
   if (c.span != g->chunk_span) {
     g->chunk_shape = rngi::rows_shape(c.span, g->opts.values_per_thread, g->opts.block_threads, g->device,
-                                      g->opts.grid_blocks);
+                                      g->opts.grid_blocks, g->opts.store_width);
     g->chunk_span = c.span;
   }
   const rngi::LaunchShape sh = g->chunk_shape;
   long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), static_cast<int>(g->opts.store_width), g->compute);
+  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute);
   op_end(g, op, g->compute);
   return rngi::cuda_fail(err, st, "rows kernel launch");
 }
@@ -390,7 +390,7 @@ void rng_opts_default(rng_opts *o) {
   o->profiling = 1;
   o->compute_stream = nullptr;
   o->device = -1;
-  o->store_policy = 0;
+  o->store_policy = 1;
   o->host_wait_ms = 0;
 }
 
@@ -441,7 +441,7 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   g->device = dev;
   g->opts = o;
   g->buf_bytes = o.device_buffer_bytes;
-  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev, o.grid_blocks);
+  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev, o.grid_blocks, o.store_width);
   rngi::live_inc();
   int rc = RNG_OK;
   if (o.compute_stream) {
@@ -526,7 +526,7 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   a.from_hash = !g->materialized;
   a.write_state = 1;
   long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), static_cast<int>(g->opts.store_width), g->compute);
+  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
   op_end(g, op, g->compute);
   rc = rngi::cuda_fail(err, st, "rows kernel launch");
   if (rc) return rc;
@@ -571,7 +571,8 @@ int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev
   a.from_hash = !g->materialized;
   a.write_state = 1;
   long op = op_begin(g, "CHECKSUM_KERNEL", kQueueMain, g->compute);
-  st = rngi::launch_checksum(a, g->shape, row_xor_dev, row_sum_dev, g->compute);
+  const uint32_t v = g->opts.values_per_thread;
+  st = rngi::launch_checksum(a, (v && (v & (v - 1)) == 0) ? v : 0, row_xor_dev, row_sum_dev, g->compute);
   op_end(g, op, g->compute);
   rc = rngi::cuda_fail(err, st, "checksum kernel launch");
   if (rc) return rc;

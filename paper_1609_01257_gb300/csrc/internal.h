@@ -39,23 +39,27 @@ struct LaunchShape {
   uint32_t vpt;
   uint32_t block;
   uint32_t grid;
+  uint32_t width;  // widest store in values (1, 2, 4) the shape may use
 };
 
 // Values-per-thread counts the row kernel is compiled for (256-thread
 // blocks), and the (values-per-thread, block) pairs of the other block sizes.
 bool rows_vpt_supported(uint32_t vpt);
 bool rows_shape_supported(uint32_t vpt, uint32_t block);
-// Picks values-per-thread (if vpt == 0), block size and a persistent grid of
-// at most max_grid blocks (0: as many as can be resident).
-LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid = 0);
-// store_policy: 0 default, 1 streaming (.cs); max_width: widest store in
-// values (1, 2, 4), 0 = widest the alignment allows.
-cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, int max_width,
-                        cudaStream_t st);
+// Picks values-per-thread (if vpt == 0), block size, store width (if width ==
+// 0) and a persistent grid of at most max_grid blocks (0: as many as can be
+// resident).
+LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid = 0,
+                       uint32_t width = 0);
+// store_policy: 0 default, 1 streaming (.cs).  Stores are the widest of
+// sh.width and what the output's alignment allows.
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st);
 cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
                         cudaStream_t st);
-cudaError_t launch_checksum(const RowsLaunch &a, const LaunchShape &sh, uint64_t *row_xor,
-                            uint64_t *row_sum, cudaStream_t st);
+// Generate-and-checksum launch; vpt = 0 picks values per thread (a power of
+// two up to 64 otherwise).
+cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,
+                            cudaStream_t st);
 int device_sm_count(int device);
 
 // Work-list kernel tables (batched and served forms).  One entry is a chunk

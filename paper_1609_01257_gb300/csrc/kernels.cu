@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "prng_math.cuh"
 
@@ -362,22 +364,38 @@ int device_sm_count(int device) {
   return sms;
 }
 
-LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid) {
+// Values per thread for 256-thread blocks, from sweeps of the row kernel on
+// GB300 (152 SMs) writing 32 GiB per point: six streams per thread (eight
+// resident blocks per SM) for large runs; in the 1M-6M stream range the
+// shapes whose tiles fill the GPU in one or two rounds were fastest.  Runs
+// too small to fill the GPU use as many threads as possible.
+uint32_t default_vpt(uint64_t streams, int sms) {
+  const uint64_t M = uint64_t(1) << 20;
+  if (streams >= 6 * M) return 6;
+  if (streams >= 7 * M / 2) return 24;
+  if (streams >= 5 * M / 2) return 6;
+  if (streams >= 2 * M) return 12;
+  if (streams >= M) return 10;
+  // Smaller runs: about four resident blocks' worth of tiles per SM.
+  const uint64_t v = streams / (uint64_t(kBlock) * 4 * static_cast<uint64_t>(sms));
+  if (v >= 8) return 8;
+  if (v >= 6) return 6;
+  if (v >= 4) return 4;
+  if (v >= 2) return 2;
+  return 1;
+}
+
+LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid,
+                       uint32_t width) {
   LaunchShape sh;
   sh.block = block ? block : kBlock;
   const int sms = device_sm_count(device);
-  if (vpt == 0) {
-    // Largest values-per-thread (<= 16) that still gives every SM at least
-    // 1024 threads of work; small runs fall back to one stream per thread.
-    vpt = 1;
-    const uint64_t want_threads = static_cast<uint64_t>(sms) * 1024;
-    for (uint32_t v = 16; v >= 2; v /= 2)
-      if (streams / v >= want_threads) {
-        vpt = v;
-        break;
-      }
-  }
+  if (vpt == 0) vpt = sh.block == kBlock ? default_vpt(streams, sms) : 8;
   sh.vpt = vpt;
+  // One 8-byte store per value measured fastest once a thread holds six or
+  // more streams (see the shape sweep in the design notes); below that the
+  // widest store the alignment allows.
+  sh.width = width ? width : (vpt >= 6 ? 1 : 4);
   const void *fn = select_rows(vpt, sh.block == kBlock ? 4 : 1, sh.block == kBlock ? kPolicyDefault : kPolicyStreaming, sh.block);
   if (!fn) {
     sh.grid = 0;
@@ -392,8 +410,7 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
   return sh;
 }
 
-cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, int max_width,
-                        cudaStream_t st) {
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st) {
   // Widest store the output's alignment allows: every row must start on an
   // 8*W-byte boundary (pitch a multiple of W, base aligned to 8*W bytes).
   int width = 1;
@@ -403,7 +420,7 @@ cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_po
       width = w;
       break;
     }
-  if (max_width > 0 && width > max_width) width = max_width;
+  if (width > static_cast<int>(sh.width)) width = static_cast<int>(sh.width);
   const void *fn = select_rows(sh.vpt, width, store_policy, sh.block);
   if (!fn) return cudaErrorInvalidValue;
   RowsLaunch args = a;
@@ -426,15 +443,32 @@ cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t 
   return e;
 }
 
-cudaError_t launch_checksum(const RowsLaunch &a, const LaunchShape &sh, uint64_t *row_xor,
-                            uint64_t *row_sum, cudaStream_t st) {
-  const void *fn = select_checksum(sh.vpt);
-  if (!fn || sh.block != kBlock) return cudaErrorInvalidValue;
+cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,
+                            cudaStream_t st) {
+  const uint64_t span = a.s_end - a.s_begin;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int sms = device_sm_count(dev);
+  if (vpt == 0) {
+    // Enough values per thread to amortise the per-row reductions, while
+    // keeping at least one tile per resident block slot.
+    vpt = 1;
+    for (uint32_t v = 16; v >= 2; v /= 2)
+      if (span / (uint64_t(kBlock) * v) >= uint64_t(sms) * 4) {
+        vpt = v;
+        break;
+      }
+  }
+  const void *fn = select_checksum(vpt);
+  if (!fn) return cudaErrorInvalidValue;
+  const uint64_t tiles = (span + uint64_t(kBlock) * vpt - 1) / (uint64_t(kBlock) * vpt);
+  const uint64_t resident = uint64_t(sms) * occupancy(fn, kBlock);
+  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(tiles, resident)));
   RowsLaunch args = a;
   unsigned long long *rx = reinterpret_cast<unsigned long long *>(row_xor);
   unsigned long long *rs = reinterpret_cast<unsigned long long *>(row_sum);
   void *params[] = {&args, &rx, &rs};
-  cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), params, 0, st);
   if (e == cudaSuccess) count_launch();
   return e;
 }

@@ -35,7 +35,7 @@ class Generator:
                  fuse_init: bool = True, stream_offset: int = 0,
                  device_buffer_bytes: int = 32 << 20, host_slots: int = 2,
                  profiling: bool = True, compute_stream=None, device: Optional[int] = None,
-                 store_policy: int = 0, host_wait_ms: int = 0, store_width: int = 0,
+                 store_policy: int = 1, host_wait_ms: int = 0, store_width: int = 0,
                  block_threads: int = 0, grid_blocks: int = 0, init: bool = True):
         lib = C.load()
         o = C.RngOpts()
