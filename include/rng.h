@@ -281,6 +281,50 @@ void *rng_batch_stream(rng_batch *b);
 void rng_batch_destroy(rng_batch *b);
 
 /* ------------------------------------------------------------------ */
+/* Batched generation without allocation                               */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc: code that runs while someone else is capturing a
+ * CUDA stream into a graph, code inside a framework whose memory pool owns
+ * the device, or latency-bound code that cannot pay for an allocation (or
+ * the device-wide synchronisation of a cudaFree) on every call.
+ *
+ * It produces exactly what rng_batch_create + rng_batch_run produce for the
+ * same instances (iterations 0 .. iterations[k]-1 of instance k into outs[k],
+ * iteration-major), with one launch of the same work-list kernel, but it
+ * allocates nothing: no cudaMalloc, cudaFree, pinned or host heap memory and
+ * no CUDA graph.  Its scratch -- the kernel's work counter and work tables --
+ * is one fixed array of RNG_NOALLOC_SCRATCH_BYTES in device global memory
+ * that every GPU loading this library holds until the process exits.
+ *
+ * Limits: at most RNG_NOALLOC_MAX_INSTANCES instances and
+ * RNG_NOALLOC_MAX_UNITS work units, one unit per started group of 2048
+ * streams of an instance (sum over k of ceil(streams[k] / 2048)); larger
+ * batches are rejected with RNG_EINVAL and a message naming the limit.
+ *
+ * Arguments are those of rng_batch_create (host arrays of `count` entries;
+ * outs[k] caller-owned device memory of 8*streams[k]*iterations[k] bytes,
+ * 8-byte aligned); `stream` is the cudaStream_t to launch on (NULL = the
+ * legacy default stream).  The call is asynchronous: it returns after
+ * queueing a table upload, a reset of the counter and the kernel on
+ * `stream`.
+ *
+ * The first call on a device, with that device current, looks up the
+ * scratch array's device address (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture begins.  All calls share the one
+ * array and each call overwrites it, so calls whose work overlaps on the GPU
+ * (launched on different streams without ordering between them) race and
+ * produce wrong output; calls on one stream are ordered and safe.  The host
+ * side of concurrent calls is serialised by a lock. */
+#define RNG_NOALLOC_MAX_INSTANCES 4096u
+#define RNG_NOALLOC_MAX_UNITS 262144u
+#define RNG_NOALLOC_SCRATCH_BYTES \
+    (256u + RNG_NOALLOC_MAX_INSTANCES * 48u + RNG_NOALLOC_MAX_UNITS * 16u)
+int rng_batch_generate_noalloc(uint32_t count, const uint64_t *streams,
+                               const uint64_t *iterations, const uint64_t *seeds,
+                               uint64_t *const *outs, void *stream, rng_err **err);
+
+/* ------------------------------------------------------------------ */
 /* Served form: continuous batching of generation requests             */
 /* ------------------------------------------------------------------ */
 /* A request asks for iterations 0 .. iterations-1 (iteration-major, the

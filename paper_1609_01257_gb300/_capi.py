@@ -131,6 +131,7 @@ SIGNATURES = {
                           P_u64, ctypes.POINTER(c_dbl)], c_int),
     "rng_batch_stream": ([c_vp], c_vp),
     "rng_batch_destroy": ([c_vp], None),
+    "rng_batch_generate_noalloc": ([c_u32, P_u64, P_u64, P_u64, ctypes.POINTER(c_vp), c_vp, P_err], c_int),
     "rng_server_opts_default": ([ctypes.POINTER(RngServerOpts)], None),
     "rng_server_create": ([ctypes.POINTER(RngServerOpts), ctypes.POINTER(c_vp), P_err], c_int),
     "rng_server_submit": ([c_vp, c_u64, c_u64, c_u64, P_u64, P_err], c_int),
