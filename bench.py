@@ -243,26 +243,39 @@ def run_gpu(args, wl):
     if not args.skip_e2e:
         host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
 
-        def step_host():
-            gen.init()
-            gen.generate_to_host(T, host)
+        def host_leg(g, steps):
+            def step_host():
+                g.init()
+                g.generate_to_host(T, host)
 
-        for _ in range(max(1, min(args.warmup, 2))):
-            step_host()
-        barrier()
-        gen.profile_reset()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            step_host()
-        barrier()
-        host_s = max_over_ranks(time.perf_counter() - t0)
-        prof = gen.profile()
+            for _ in range(max(1, min(args.warmup, 2))):
+                step_host()
+            barrier()
+            g.profile_reset()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                step_host()
+            barrier()
+            return max_over_ranks(time.perf_counter() - t0), g.profile()
+
+        # Default host path: the kernel stores straight into the page-locked
+        # buffer over the host link.
+        host_s, _ = host_leg(gen, args.e2e_steps)
         e2e = {"value": nbytes * ws * args.e2e_steps / host_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes,
                "steps": args.e2e_steps, "ms_per_step": 1e3 * host_s / args.e2e_steps,
-               "read_buffer_s": prof["aggregate"].get("READ_BUFFER", (0, 0))[0] / args.e2e_steps,
-               "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0] / args.e2e_steps,
-               "overlap_s": sum(prof["overlaps"].values()) / args.e2e_steps}
+               "path": "direct stores into page-locked host memory"}
+        # The paper's double buffer: two device buffers, copy engine reads.
+        gdb = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+                            host_path=1, init=False)
+        db_s, prof = host_leg(gdb, args.e2e_steps)
+        gdb.close()
+        e2e["double_buffer"] = {
+            "value": nbytes * ws * args.e2e_steps / db_s / 1e9, "unit": "GB/s",
+            "ms_per_step": 1e3 * db_s / args.e2e_steps,
+            "read_buffer_s": prof["aggregate"].get("READ_BUFFER", (0, 0))[0] / args.e2e_steps,
+            "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0] / args.e2e_steps,
+            "overlap_s": sum(prof["overlaps"].values()) / args.e2e_steps}
         del host
 
     gen.close()
@@ -302,13 +315,140 @@ def run_gpu(args, wl):
     return 0
 
 
+def _json_line(d):
+    print(json.dumps(d), flush=True)
+
+
+def run_batched(args):
+    """Batched form: 512 independent instances (log-uniform sizes, 8 GiB total)
+    in one CUDA-graph launch, against the plain form (one generator and one
+    launch per instance) on the same GPU."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+    import workloads
+
+    inst = workloads.batched_instances()
+    total = sum(i.nbytes for i in inst)
+    b = rng.Batch([i.streams for i in inst], [i.iterations for i in inst], [i.seed for i in inst])
+    cfg = b.config()
+    s = b.stream
+    for _ in range(args.warmup):
+        b.run()
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        b.run()
+    e1.record(s)
+    e1.synchronize()
+    batched_s = e0.elapsed_time(e1) * 1e-3 / args.steps
+    # Plain form: one generator per instance, launched one after another.
+    plain_stream = torch.cuda.Stream()
+    gens = [rng.Generator(i.streams, i.seed, compute_stream=plain_stream, profiling=False, init=False)
+            for i in inst]
+
+    def plain_step():
+        for g, o, i in zip(gens, b.outputs, inst):
+            g.init()
+            g.generate_to(i.iterations, o.data_ptr())
+
+    for _ in range(args.warmup):
+        plain_step()
+    plain_stream.synchronize()
+    e0.record(plain_stream)
+    for _ in range(args.steps):
+        plain_step()
+    e1.record(plain_stream)
+    e1.synchronize()
+    plain_s = e0.elapsed_time(e1) * 1e-3 / args.steps
+    for g in gens:
+        g.close()
+    b.close()
+    _json_line({"workload": "batched: 512 instances, streams log-uniform [2^8, 2^20], iterations log-uniform "
+                            "[1, 4096] capped at 8 GiB, seeds splitmix64 from 7",
+                "bytes_per_step": total, "batched_GBps": total / batched_s / 1e9, "batched_ms": batched_s * 1e3,
+                "plain_GBps": total / plain_s / 1e9, "plain_ms": plain_s * 1e3, "tuned": cfg,
+                "steps": args.steps, "warmup": args.warmup})
+    return 0
+
+
+def run_served(args):
+    """Served form: Poisson arrivals (2000/s), continuous batching, 64 GiB budget."""
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+    import workloads
+
+    reqs = workloads.served_requests(duration_s=args.duration)
+    offered = sum(r.nbytes for r in reqs)
+    with rng.Server(hbm_budget_bytes=64 << 30) as srv:
+        warm = workloads.served_requests(duration_s=0.5, seed_start=5, arrival_start=6, size_start=7)
+        rng.run_load(srv, warm)
+        res = rng.run_load(srv, reqs)
+        st = srv.stats()
+    _json_line({"workload": f"served: Poisson 2000 req/s for {args.duration:g} s, streams log-uniform [2^10, 2^22], "
+                            "iterations log-uniform [1, 512], seeds splitmix64 from 99, 64 GiB budget",
+                "requests": len(reqs), "p50_ms": res.percentile(50) * 1e3, "p99_ms": res.percentile(99) * 1e3,
+                "max_ms": max(res.latencies_s.values()) * 1e3,
+                "aggregate_GBps": res.bytes / res.wall_s / 1e9, "offered_GBps": offered / args.duration / 1e9,
+                "wall_s": res.wall_s, "worst_submit_lag_ms": res.submit_lag_s * 1e3,
+                "steps": st["steps"], "peak_active": st["peak_active"],
+                "peak_bytes_in_use": st["peak_bytes_in_use"]})
+    return 0
+
+
+def run_sweep(args):
+    """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread,
+    output into a ring of two 2 GiB device buffers, >= 16 GiB per point;
+    and generate-and-checksum mode per stream count."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    ring = [torch.empty(GIB // 4, dtype=torch.uint64, device="cuda") for _ in range(2)]
+    for e in range(16, 29, 2):
+        n = 1 << e
+        rows = max(1, (2 * GIB) // (8 * n))
+        launches = max(2, -(-(16 * GIB) // (8 * n * rows)))
+        res = {}
+        for vpt in args.sweep_vpts:
+            g = rng.Generator(n, 1, values_per_thread=vpt, init=False)
+            g.init()
+            for k in range(3):
+                g.generate_to(rows, ring[k & 1].data_ptr())
+            g.sync()
+            g.profile_reset()
+            for k in range(launches):
+                g.generate_to(rows, ring[k & 1].data_ptr())
+            c, t = g.profile_stat("RNG_KERNEL")
+            res[vpt] = 8 * n * rows * c / t / 1e9
+            g.close()
+        g = rng.Generator(n, 1, init=False)
+        g.init()
+        auto = g.launch_config()
+        ck_rows = max(1, (16 * GIB) // (8 * n))
+        g.generate_checksum(ck_rows)
+        g.sync()
+        g.profile_reset()
+        g.generate_checksum(ck_rows)
+        c, t = g.profile_stat("CHECKSUM_KERNEL")
+        g.close()
+        _json_line({"sweep_streams": n, "rows_per_launch": rows, "launches": launches,
+                    "write_GBps_by_vpt": {str(k): round(v, 1) for k, v in res.items()},
+                    "default_shape": {"vpt": auto[0], "grid": auto[2]},
+                    "checksum_values_per_s": n * ck_rows / t, "checksum_equiv_GBps": 8 * n * ck_rows / t / 1e9})
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="streaming")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep"], default="streaming")
+    ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
+    ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
@@ -319,6 +459,12 @@ def main(argv=None):
                     help="override the workload's iteration count (profiling captures of a smaller case)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     wl = dict(WORKLOADS[args.workload])
     if args.iterations:
         wl["iterations"] = args.iterations

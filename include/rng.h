@@ -100,6 +100,14 @@ typedef struct rng_opts {
                                      thread, else 4) */
     uint32_t grid_blocks;         /* cap on the persistent grid; 0 = every block
                                      that can be resident */
+    uint32_t host_path;           /* host output: 0 = direct when the GPU can
+                                     store into the destination (page-locked
+                                     memory, or pageable memory on systems with
+                                     pageable access such as Grace over
+                                     NVLink-C2C), else double buffer;
+                                     1 = always the double buffer of Section 5;
+                                     2 = always direct (RNG_EINVAL if the GPU
+                                     cannot store into the destination) */
 } rng_opts;
 
 void rng_opts_default(rng_opts *opts);
@@ -132,12 +140,15 @@ int rng_init(rng_gen *g, rng_err **err);
  *    value (it - p) * streams + g.  Ordered on the compute stream; returns
  *    before the kernel completes.
  *  - out_host: caller-owned host memory of 8*streams*iterations bytes in
- *    the same layout.  Values are produced in two device buffers that
- *    alternate (generation into one while the other is copied to the host
- *    on a separate copy stream, ordered by CUDA events).  Page-locked
- *    memory is written directly by the copy engine; pageable memory goes
- *    through the library's pinned staging slots.  Blocks until every value
- *    is in out_host (the paper's blocking read).
+ *    the same layout.  Double-buffer path (Section 5): values are produced
+ *    in two device buffers that alternate (generation into one while the
+ *    other is copied to the host on a separate copy stream, ordered by CUDA
+ *    events); page-locked memory is written directly by the copy engine,
+ *    pageable memory goes through the library's pinned staging slots.
+ *    Direct path: the kernel stores the values into the host memory itself
+ *    over the host link, with no device buffer and no copy (see
+ *    rng_opts.host_path).  Blocks until every value is in out_host (the
+ *    paper's blocking read).
  * iterations == 0 is a no-op.  Errors: RNG_EINVAL (both or neither output,
  * size overflow), RNG_ESTATE (not initialised), RNG_ECUDA. */
 int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev,

@@ -44,6 +44,7 @@ class RngOpts(ctypes.Structure):
         ("host_wait_ms", c_u32),
         ("store_width", c_u32),
         ("grid_blocks", c_u32),
+        ("host_path", c_u32),
     ]
 
 

@@ -262,7 +262,7 @@ struct Consumer {
   }
 };
 
-int staged_or_direct(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn sink, void *user,
+int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn sink, void *user,
                      rng_err **err) {
   bool pinned = false;
   if (out_host) {
@@ -360,6 +360,55 @@ int staged_or_direct(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn sin
   return RNG_OK;
 }
 
+// Whether kernels on g's device can store into host memory at `p`: page-locked
+// (registered) memory always can under unified addressing; pageable memory
+// only where the device reads the host's page tables (e.g. Grace over
+// NVLink-C2C).  *dev_ptr receives the address to use in kernels.
+bool device_can_store(rng_gen *g, uint64_t *p, uint64_t **dev_ptr) {
+  cudaPointerAttributes attr;
+  cudaError_t st = cudaPointerGetAttributes(&attr, p);
+  if (st != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (attr.type == cudaMemoryTypeHost) {
+    *dev_ptr = static_cast<uint64_t *>(attr.devicePointer ? attr.devicePointer : p);
+    return true;
+  }
+  if (attr.type == cudaMemoryTypeUnregistered) {
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, g->device) == cudaSuccess &&
+        pageable) {
+      *dev_ptr = p;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Direct path: one launch stores all rows into host memory over the link.
+int direct_host(rng_gen *g, uint64_t T, uint64_t *dst, rng_err **err) {
+  rngi::RowsLaunch a{};
+  a.state = g->d_state;
+  a.out = dst;
+  a.pitch = g->n;
+  a.s_begin = 0;
+  a.s_end = g->n;
+  a.id_base = g->g0;
+  a.rows = T;
+  a.key = g->key;
+  a.from_hash = !g->materialized;
+  a.write_state = 1;
+  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
+  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
+  op_end(g, op, g->compute);
+  int rc = rngi::cuda_fail(err, st, "rows kernel launch (direct to host)");
+  if (rc) return rc;
+  g->materialized = true;
+  g->pos += T;
+  return rngi::cuda_fail(err, cudaStreamSynchronize(g->compute), "cudaStreamSynchronize(direct to host)");
+}
+
 int check_gen(const rng_gen *g, rng_err **err, const char *fn) {
   if (!g) return rngi::fail(err, RNG_EINVAL, "%s: NULL generator", fn);
   if (cudaSetDevice(g->device) != cudaSuccess)
@@ -419,6 +468,7 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   if (o.device_buffer_bytes < 16 || o.device_buffer_bytes % 16)
     return rngi::fail(err, RNG_EINVAL, "rng_create: device_buffer_bytes must be a positive multiple of 16");
   if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
+  if (o.host_path > 2) return rngi::fail(err, RNG_EINVAL, "rng_create: host_path must be 0, 1 or 2");
   if (o.store_width != 0 && o.store_width != 1 && o.store_width != 2 && o.store_width != 4)
     return rngi::fail(err, RNG_EINVAL, "rng_create: store_width must be 0, 1, 2 or 4");
   if (o.stream_offset > (uint64_t(1) << 32) - streams)
@@ -511,7 +561,14 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   if (iterations == 0) return RNG_OK;
   rc = size_ok(g->n, iterations, err);
   if (rc) return rc;
-  if (out_host) return staged_or_direct(g, iterations, out_host, nullptr, nullptr, err);
+  if (out_host) {
+    uint64_t *dptr = nullptr;
+    const bool can = g->opts.host_path != 1 && device_can_store(g, out_host, &dptr);
+    if (g->opts.host_path == 2 && !can)
+      return rngi::fail(err, RNG_EINVAL, "rng_generate: the GPU cannot store into this host memory (host_path = 2)");
+    if (can) return direct_host(g, iterations, dptr, err);
+    return double_buffer_host(g, iterations, out_host, nullptr, nullptr, err);
+  }
   if (reinterpret_cast<uintptr_t>(out_dev) % 8)
     return rngi::fail(err, RNG_EINVAL, "rng_generate: out_dev must be 8-byte aligned");
   rngi::RowsLaunch a{};
@@ -543,7 +600,7 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink, void *u
   if (iterations == 0) return RNG_OK;
   rc = size_ok(g->n, iterations, err);
   if (rc) return rc;
-  return staged_or_direct(g, iterations, nullptr, sink, user, err);
+  return double_buffer_host(g, iterations, nullptr, sink, user, err);
 }
 
 int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev, uint64_t *row_sum_dev,

@@ -146,11 +146,14 @@ def test_no_write_outside_output():
     assert np.array_equal(r[pad:-pad].view(np.uint64).reshape(T, n), oracle.generate(n, 8, T))
 
 
+@pytest.mark.parametrize("host_path", [0, 1])
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("n,T,buf", [(4096, 40, 1 << 16), (3001, 7, 8 * 3001 * 2), (5000, 3, 4096), (7, 100, 64)])
-def test_host_output(pinned, n, T, buf):
-    # buf smaller than one row (5000 streams x 8 B > 4096) exercises column slabs.
-    g = rng.Generator(n, 4, device_buffer_bytes=buf)
+def test_host_output(host_path, pinned, n, T, buf):
+    # host_path 1: the double buffer; buf smaller than one row (5000 streams x
+    # 8 B > 4096) exercises column slabs.  host_path 0: direct stores where
+    # the GPU can reach the destination.
+    g = rng.Generator(n, 4, device_buffer_bytes=buf, host_path=host_path)
     out = torch.empty((T, n), dtype=torch.uint64)
     if pinned:
         out = out.pin_memory()
@@ -164,8 +167,9 @@ def test_host_output(pinned, n, T, buf):
     assert np.array_equal(second, want[T:])
 
 
-def test_device_then_host_then_device():
-    g = rng.Generator(2048, 9, device_buffer_bytes=8 * 2048 * 3)
+@pytest.mark.parametrize("host_path", [0, 1])
+def test_device_then_host_then_device(host_path):
+    g = rng.Generator(2048, 9, device_buffer_bytes=8 * 2048 * 3, host_path=host_path)
     a = g.generate(4).cpu().numpy()
     b = g.generate_to_host(10)
     c = g.generate(2).cpu().numpy()
@@ -237,7 +241,7 @@ def test_checksum_mode(n, T):
 
 def test_profiler_names_and_overlap():
     n = 1 << 18
-    g = rng.Generator(n, 1, device_buffer_bytes=8 * n, fuse_init=False)
+    g = rng.Generator(n, 1, device_buffer_bytes=8 * n, fuse_init=False, host_path=1)
     g.profile_reset()
     g.init()
     g.generate_to_host(8)
@@ -251,6 +255,19 @@ def test_profiler_names_and_overlap():
     assert p["effective"] <= p["total"] + 1e-12
     assert p["effective"] <= p["elapsed"]
     assert "Aggregate times by event" in s and "Time spent in device" in s
+
+
+def test_direct_path_records_one_kernel_and_no_copy():
+    n = 1 << 16
+    host = torch.empty((6, n), dtype=torch.uint64).pin_memory()
+    g = rng.Generator(n, 3, host_path=2)
+    g.profile_reset()
+    g.generate_to_host(6, host)
+    cnt_k, _ = g.profile_stat("RNG_KERNEL")
+    cnt_r, _ = g.profile_stat("READ_BUFFER")
+    g.close()
+    assert (cnt_k, cnt_r) == (1, 0)
+    assert np.array_equal(host.numpy(), oracle.generate(n, 3, 6))
 
 
 def test_live_objects_balance():
