@@ -397,46 +397,100 @@ def run_served(args):
     return 0
 
 
-def run_sweep(args):
-    """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread,
-    output into a ring of two 2 GiB device buffers, >= 16 GiB per point;
-    and generate-and-checksum mode per stream count."""
+def run_checksum(args, wl):
+    """Generate-and-checksum mode on the streaming workload: every value is
+    produced and folded into its row's XOR and wrapping sum; nothing is
+    stored.  Bound by integer issue, not memory."""
     import torch
     sys.path.insert(0, ROOT)
     import paper_1609_01257_gb300 as rng
 
-    ring = [torch.empty(GIB // 4, dtype=torch.uint64, device="cuda") for _ in range(2)]
+    n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
+    g = rng.Generator(n, seed, init=False)
+    rx = torch.empty(T, dtype=torch.uint64, device="cuda")
+    rs = torch.empty(T, dtype=torch.uint64, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        g.init()
+        g.generate_checksum(T, rx, rs)
+
+    for _ in range(args.warmup):
+        step()
+    g.sync()
+    g.profile_reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = g.stream
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) * 1e-3
+    c, t = g.profile_stat("CHECKSUM_KERNEL")
+    g.close()
+    props = torch.cuda.get_device_properties(0)
+    vps = n * T * args.steps / secs
+    _json_line({"workload": wl["name"] + " (generate-and-checksum mode)", "values_per_s": vps,
+                "equiv_GBps": 8 * vps / 1e9, "kernel_avg_ms": 1e3 * t / max(c, 1), "steps": args.steps,
+                "sms": props.multi_processor_count,
+                "note": "ALU roofline: thread-instructions per value from the ncu summary x values/s, "
+                        "against SMs x 128 lanes x SM clock"})
+    return 0
+
+
+def run_sweep(args):
+    """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread.
+    Output goes to a ring of two 2 GiB device buffers: each launch writes the
+    whole 4 GiB ring once (iterations = ring rows, no row written twice in a
+    launch, so L2 cannot absorb rewrites), four launches per point (16 GiB).
+    Launches carry the states through the state array (8 B read + 8 B written
+    per stream per launch), reported separately as `dram_GBps_incl_state`.
+    Generate-and-checksum mode is timed per stream count as well."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    ring = torch.empty(GIB // 2, dtype=torch.uint64, device="cuda")  # 2 x 2 GiB
+    launches = 4
     for e in range(16, 29, 2):
         n = 1 << e
-        rows = max(1, (2 * GIB) // (8 * n))
-        launches = max(2, -(-(16 * GIB) // (8 * n * rows)))
-        res = {}
-        for vpt in args.sweep_vpts:
-            g = rng.Generator(n, 1, values_per_thread=vpt, init=False)
+        rows = (4 * GIB) // (8 * n)
+        out = ring[: rows * n]
+        res, res_dram = {}, {}
+
+        def point(**kw):
+            g = rng.Generator(n, 1, init=False, **kw)
             g.init()
-            for k in range(3):
-                g.generate_to(rows, ring[k & 1].data_ptr())
+            g.generate_to(rows, out.data_ptr())
             g.sync()
             g.profile_reset()
-            for k in range(launches):
-                g.generate_to(rows, ring[k & 1].data_ptr())
+            for _ in range(launches):
+                g.generate_to(rows, out.data_ptr())
             c, t = g.profile_stat("RNG_KERNEL")
-            res[vpt] = 8 * n * rows * c / t / 1e9
+            cfg = g.launch_config()
             g.close()
-        g = rng.Generator(n, 1, init=False)
-        g.init()
-        auto = g.launch_config()
-        ck_rows = max(1, (16 * GIB) // (8 * n))
-        g.generate_checksum(ck_rows)
-        g.sync()
-        g.profile_reset()
-        g.generate_checksum(ck_rows)
-        c, t = g.profile_stat("CHECKSUM_KERNEL")
-        g.close()
+            return 8 * n * rows * c / t / 1e9, (8 * n * rows + 16 * n) * c / t / 1e9, cfg
+
+        for vpt in args.sweep_vpts:
+            res[vpt], res_dram[vpt], _ = point(values_per_thread=vpt)
+        dflt, dflt_dram, cfg = point()
+        ck = rng.Generator(n, 1, init=False)
+        ck.init()
+        T = max(1, (16 * GIB) // (8 * n))
+        ck.generate_checksum(T)
+        ck.sync()
+        ck.profile_reset()
+        ck.generate_checksum(T)
+        c, t = ck.profile_stat("CHECKSUM_KERNEL")
+        ck.close()
         _json_line({"sweep_streams": n, "rows_per_launch": rows, "launches": launches,
                     "write_GBps_by_vpt": {str(k): round(v, 1) for k, v in res.items()},
-                    "default_shape": {"vpt": auto[0], "grid": auto[2]},
-                    "checksum_values_per_s": n * ck_rows / t, "checksum_equiv_GBps": 8 * n * ck_rows / t / 1e9})
+                    "dram_GBps_incl_state_by_vpt": {str(k): round(v, 1) for k, v in res_dram.items()},
+                    "default_shape": {"vpt": cfg[0], "grid": cfg[2], "GBps": round(dflt, 1),
+                                      "dram_GBps_incl_state": round(dflt_dram, 1)},
+                    "checksum_iterations": T, "checksum_values_per_s": n * T / t,
+                    "checksum_equiv_GBps": 8 * n * T / t / 1e9})
     return 0
 
 
@@ -446,7 +500,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep"], default="streaming")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum"], default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -465,10 +519,12 @@ def main(argv=None):
         return run_served(args)
     if args.workload == "sweep":
         return run_sweep(args)
-    wl = dict(WORKLOADS[args.workload])
+    wl = dict(WORKLOADS["streaming" if args.workload == "checksum" else args.workload])
     if args.iterations:
         wl["iterations"] = args.iterations
         wl["name"] = re.sub(r"x \d+ iterations", f"x {args.iterations} iterations", wl["name"])
+    if args.workload == "checksum":
+        return run_checksum(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

@@ -72,8 +72,8 @@ uint64_t rng_launch_count(void);
 /* ------------------------------------------------------------------ */
 typedef struct rng_opts {
     uint32_t struct_size;         /* sizeof(rng_opts), set by rng_opts_default */
-    uint32_t values_per_thread;   /* streams per GPU thread: 1-8, 10, 12, 14, 16, 20,
-                                     24, 28, 32, 48 or 64; 0 = choose */
+    uint32_t values_per_thread;   /* streams per GPU thread: 1-8, 10, 12, ... 28
+                                     (even), 32, 36, 40, 48 or 64; 0 = choose */
     uint32_t block_threads;       /* threads per block: 256 (0 = 256), or 128, 512,
                                      1024 with values_per_thread 2, 4, 6, 8, 12,
                                      16 or 24 (one 8-byte streaming store per value) */
@@ -98,8 +98,9 @@ typedef struct rng_opts {
                                      output's alignment may force narrower);
                                      0 = per shape (1 for >= 6 values per
                                      thread, else 4) */
-    uint32_t grid_blocks;         /* cap on the persistent grid; 0 = every block
-                                     that can be resident */
+    uint32_t grid_blocks;         /* blocks of the row kernel's grid; 0 = one per
+                                     tile of block_threads x values_per_thread
+                                     streams; fewer: blocks stride over tiles */
     uint32_t host_path;           /* host output: 0 = direct when the GPU can
                                      store into the destination (page-locked
                                      memory, or pageable memory on systems with
@@ -153,6 +154,16 @@ int rng_init(rng_gen *g, rng_err **err);
  * size overflow), RNG_ESTATE (not initialised), RNG_ECUDA. */
 int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev,
                  uint64_t *out_host, rng_err **err);
+
+/* Like rng_generate with device output, but into a ring of `ring_rows`
+ * rows (ring_dev: caller-owned device memory of 8*streams*ring_rows bytes):
+ * iteration p+i goes to row i mod ring_rows, so rows are overwritten within
+ * the call and the ring ends up holding the last min(iterations, ring_rows)
+ * iterations.  For consumers that only need the most recent rows, and for
+ * measuring generation over more iterations than fit in memory.  One kernel
+ * launch; ordered on the compute stream. */
+int rng_generate_ring(rng_gen *g, uint64_t iterations, uint64_t *ring_dev,
+                      uint64_t ring_rows, rng_err **err);
 
 /* Host consumer ("out" block of Section 5).  Called on a library thread,
  * in order, once per chunk of finished values: `values` holds `rows`

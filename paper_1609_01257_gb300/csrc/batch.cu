@@ -129,8 +129,9 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     o = *opts;
   }
   const uint32_t v = o.values_per_thread;
-  if (v && (v > 32 || (v & (v - 1))))
-    return rngi::fail(err, RNG_EINVAL, "rng_batch_create: values_per_thread must be 0 or 1..32 (power of two)");
+  if (v && !rngi::batch_vpt_supported(v))
+    return rngi::fail(err, RNG_EINVAL,
+                      "rng_batch_create: values_per_thread must be 0 or one of 1, 2, 4, 6, 8, 12, 16, 24, 32");
   if (o.block_threads && o.block_threads != kBlock)
     return rngi::fail(err, RNG_EINVAL, "rng_batch_create: block_threads must be 0 or 256");
   for (uint32_t k = 0; k < count; ++k) {
@@ -184,7 +185,8 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     const uint32_t reps = o.tune_reps ? o.tune_reps : 3;
     uint32_t best_v = 0;
     double best_ms = 0.0;
-    for (uint32_t cand = 1; cand <= 32 && !rc; cand *= 2) {
+    for (uint32_t cand : {1u, 2u, 4u, 6u, 8u, 12u, 16u, 24u, 32u}) {
+      if (rc) break;
       rc = prepare(b, cand, err);
       if (!rc) rc = replay(b, err);  // warm-up
       if (!rc) rc = rngi::cuda_fail(err, cudaEventRecord(e0, b->stream), "cudaEventRecord");

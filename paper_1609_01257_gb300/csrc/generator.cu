@@ -184,7 +184,8 @@ int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_
   a.write_state = 1;
   if (c.span != g->chunk_span) {
     g->chunk_shape = rngi::rows_shape(c.span, g->opts.values_per_thread, g->opts.block_threads, g->device,
-                                      g->opts.grid_blocks, g->opts.store_width);
+                                      g->opts.grid_blocks, g->opts.store_width,
+                                      static_cast<int>(g->opts.store_policy));
     g->chunk_span = c.span;
   }
   const rngi::LaunchShape sh = g->chunk_shape;
@@ -491,7 +492,8 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   g->device = dev;
   g->opts = o;
   g->buf_bytes = o.device_buffer_bytes;
-  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev, o.grid_blocks, o.store_width);
+  g->shape = rngi::rows_shape(streams, o.values_per_thread, o.block_threads, dev, o.grid_blocks, o.store_width,
+                              static_cast<int>(o.store_policy));
   rngi::live_inc();
   int rc = RNG_OK;
   if (o.compute_stream) {
@@ -586,6 +588,38 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
   op_end(g, op, g->compute);
   rc = rngi::cuda_fail(err, st, "rows kernel launch");
+  if (rc) return rc;
+  g->materialized = true;
+  g->pos += iterations;
+  return RNG_OK;
+}
+
+int rng_generate_ring(rng_gen *g, uint64_t iterations, uint64_t *ring_dev, uint64_t ring_rows, rng_err **err) {
+  int rc = check_gen(g, err, "rng_generate_ring");
+  if (rc) return rc;
+  if (!ring_dev || ring_rows == 0) return rngi::fail(err, RNG_EINVAL, "rng_generate_ring: NULL ring or zero rows");
+  if (reinterpret_cast<uintptr_t>(ring_dev) % 8)
+    return rngi::fail(err, RNG_EINVAL, "rng_generate_ring: ring must be 8-byte aligned");
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_generate_ring: generator not initialised (call rng_init)");
+  if (iterations == 0) return RNG_OK;
+  rc = size_ok(g->n, ring_rows, err);
+  if (rc) return rc;
+  rngi::RowsLaunch a{};
+  a.state = g->d_state;
+  a.out = ring_dev;
+  a.pitch = g->n;
+  a.s_begin = 0;
+  a.s_end = g->n;
+  a.id_base = g->g0;
+  a.rows = iterations;
+  a.key = g->key;
+  a.from_hash = !g->materialized;
+  a.write_state = 1;
+  a.ring_rows = ring_rows;
+  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
+  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
+  op_end(g, op, g->compute);
+  rc = rngi::cuda_fail(err, st, "rows kernel launch (ring)");
   if (rc) return rc;
   g->materialized = true;
   g->pos += iterations;

@@ -33,6 +33,7 @@ struct RowsLaunch {
   uint32_t key;
   int from_hash;        // initial state from the hash instead of `state`
   int write_state;      // store the advanced states back
+  uint64_t ring_rows;   // 0, or rows wrap around a ring of this many rows
 };
 
 struct LaunchShape {
@@ -47,10 +48,10 @@ struct LaunchShape {
 bool rows_vpt_supported(uint32_t vpt);
 bool rows_shape_supported(uint32_t vpt, uint32_t block);
 // Picks values-per-thread (if vpt == 0), block size, store width (if width ==
-// 0) and a persistent grid of at most max_grid blocks (0: as many as can be
-// resident).
+// 0) and the grid: one block per tile, or max_grid blocks if set (blocks then
+// stride over tiles).  `policy` names the variant that will run.
 LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid = 0,
-                       uint32_t width = 0);
+                       uint32_t width = 0, int policy = 1);
 // store_policy: 0 default, 1 streaming (.cs).  Stores are the widest of
 // sh.width and what the output's alignment allows.
 cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st);
@@ -86,5 +87,7 @@ cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint
                          uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
                          cudaStream_t st);
 int batch_blocks_per_sm(uint32_t vpt, uint32_t block);
+// Values per thread the work-list kernel is compiled for.
+bool batch_vpt_supported(uint32_t vpt);
 
 }  // namespace rngi

@@ -71,11 +71,15 @@ __device__ __forceinline__ uint64_t slot_offset(int j, int q) {
 
 // Emits `rows` rows of one tile, W values per store.  CHECK: some values of
 // the tile lie past the end of the stream range and must not be stored.
+// ring != 0: rows wrap around a ring of `ring` rows starting at `row`.
 template <int VPT, int W, int POLICY, bool CHECK, int BLOCK = kBlock>
 __device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, uint64_t pitch,
-                                          uint64_t rows, uint64_t rel0, uint64_t span) {
+                                          uint64_t rows, uint64_t rel0, uint64_t span,
+                                          uint64_t ring = 0) {
   constexpr int J = VPT / W;
-  for (uint64_t r = 0; r < rows; ++r, row += pitch) {
+  uint64_t *const first = row;
+  uint64_t in_ring = 0;
+  for (uint64_t r = 0; r < rows; ++r) {
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       const uint64_t rel = rel0 + slot_offset<W, BLOCK>(j, 0);
@@ -89,6 +93,11 @@ __device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, ui
     }
 #pragma unroll
     for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+    row += pitch;
+    if (ring && ++in_ring == ring) {
+      row = first;
+      in_ring = 0;
+    }
   }
 }
 
@@ -132,9 +141,9 @@ __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
     load_tile<VPT, W, BLOCK>(st, a, rel0, span);
     if (a.out) {
       if (rel0 + tile_vals <= span)
-        emit_rows<VPT, W, POLICY, false, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span);
+        emit_rows<VPT, W, POLICY, false, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
       else
-        emit_rows<VPT, W, POLICY, true, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span);
+        emit_rows<VPT, W, POLICY, true, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
     } else {
       for (uint64_t r = 0; r < a.rows; ++r)
 #pragma unroll
@@ -246,22 +255,25 @@ __global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *_
     const uint64_t span = wu.count;
     const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
     uint64_t *row = in.out + wu.s_begin;
-    if (VPT % 2 == 0 && in.vec) {
+    // 16-byte stores for few values per thread on aligned rows; one
+    // streaming 8-byte store per value otherwise (the faster form once a
+    // thread holds six or more streams).
+    if (VPT % 2 == 0 && VPT < 6 && in.vec) {
       constexpr int V2 = VPT >= 2 ? VPT : 2;
       uint64_t st[V2];
       load_tile<V2, 2>(st, a, 0, span);
       if (span == tile_vals)
-        emit_rows<V2, 2, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<V2, 2, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
       else
-        emit_rows<V2, 2, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<V2, 2, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
       if (a.write_state) store_tile_state<V2, 2>(st, a, 0, span);
     } else {
       uint64_t st[VPT];
       load_tile<VPT, 1>(st, a, 0, span);
       if (span == tile_vals)
-        emit_rows<VPT, 1, kPolicyDefault, false>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<VPT, 1, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
       else
-        emit_rows<VPT, 1, kPolicyDefault, true>(st, row, a.pitch, a.rows, 0, span);
+        emit_rows<VPT, 1, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
       if (a.write_state) store_tile_state<VPT, 1>(st, a, 0, span);
     }
   }
@@ -303,7 +315,8 @@ const void *rows_fn_dispatch(int width, int policy) {
 }
 
 #define RNG_FOR_EACH_VPT(X) \
-  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14) X(16) X(20) X(24) X(28) X(32) X(48) X(64)
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) \
+  X(32) X(36) X(40) X(48) X(64)
 
 const void *select_rows(uint32_t vpt, int width, int policy, uint32_t block = kBlock) {
   if (block == 512) return rows_fn_wide<512>(vpt);
@@ -339,8 +352,11 @@ const void *select_batch(uint32_t vpt) {
     case 1: return reinterpret_cast<const void *>(&worklist_kernel<1>);
     case 2: return reinterpret_cast<const void *>(&worklist_kernel<2>);
     case 4: return reinterpret_cast<const void *>(&worklist_kernel<4>);
+    case 6: return reinterpret_cast<const void *>(&worklist_kernel<6>);
     case 8: return reinterpret_cast<const void *>(&worklist_kernel<8>);
+    case 12: return reinterpret_cast<const void *>(&worklist_kernel<12>);
     case 16: return reinterpret_cast<const void *>(&worklist_kernel<16>);
+    case 24: return reinterpret_cast<const void *>(&worklist_kernel<24>);
     case 32: return reinterpret_cast<const void *>(&worklist_kernel<32>);
     default: return nullptr;
   }
@@ -365,28 +381,26 @@ int device_sm_count(int device) {
 }
 
 // Values per thread for 256-thread blocks, from sweeps of the row kernel on
-// GB300 (152 SMs) writing 32 GiB per point: six streams per thread (eight
-// resident blocks per SM) for large runs; in the 1M-6M stream range the
-// shapes whose tiles fill the GPU in one or two rounds were fastest.  Runs
-// too small to fill the GPU use as many threads as possible.
+// GB300 (152 SMs) writing 32 GiB per point with one tile per block: 24
+// streams per thread (one 48 KiB run per block and row, one resident block
+// per SM) was fastest from 2^22 to 2^26 streams; 12 around 2^21; 32 at 2^20,
+// where 128 tiles still cover most SMs.  Smaller runs use as many threads as
+// give about one to two tiles per SM.
 uint32_t default_vpt(uint64_t streams, int sms) {
   const uint64_t M = uint64_t(1) << 20;
-  if (streams >= 6 * M) return 6;
   if (streams >= 7 * M / 2) return 24;
-  if (streams >= 5 * M / 2) return 6;
-  if (streams >= 2 * M) return 12;
-  if (streams >= M) return 10;
-  // Smaller runs: about four resident blocks' worth of tiles per SM.
-  const uint64_t v = streams / (uint64_t(kBlock) * 4 * static_cast<uint64_t>(sms));
+  if (streams >= 3 * M / 2) return 12;
+  if (streams >= 3 * M / 4) return 32;
+  const uint64_t v = streams / (uint64_t(kBlock) * static_cast<uint64_t>(sms));
+  if (v >= 16) return 16;
   if (v >= 8) return 8;
-  if (v >= 6) return 6;
   if (v >= 4) return 4;
   if (v >= 2) return 2;
   return 1;
 }
 
 LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid,
-                       uint32_t width) {
+                       uint32_t width, int policy) {
   LaunchShape sh;
   sh.block = block ? block : kBlock;
   const int sms = device_sm_count(device);
@@ -396,16 +410,22 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
   // more streams (see the shape sweep in the design notes); below that the
   // widest store the alignment allows.
   sh.width = width ? width : (vpt >= 6 ? 1 : 4);
-  const void *fn = select_rows(vpt, sh.block == kBlock ? 4 : 1, sh.block == kBlock ? kPolicyDefault : kPolicyStreaming, sh.block);
+  // Occupancy of the variant that will run (policy and store width change
+  // the register count).
+  const void *fn = select_rows(vpt, static_cast<int>(sh.width), sh.block == kBlock ? policy : kPolicyStreaming, sh.block);
   if (!fn) {
     sh.grid = 0;
     return sh;
   }
   const uint64_t tiles = (streams + static_cast<uint64_t>(sh.block) * vpt - 1) /
                          (static_cast<uint64_t>(sh.block) * vpt);
-  const uint64_t resident = static_cast<uint64_t>(sms) * occupancy(fn, sh.block);
-  uint64_t grid = tiles < resident ? tiles : resident;
-  if (max_grid && grid > max_grid) grid = max_grid;
+  // One block per tile by default: the hardware hands tiles out in order as
+  // blocks finish, which measured ~10% faster than a persistent grid-stride
+  // loop (tiles running at the same time stay adjacent in memory).  max_grid
+  // asks for fewer blocks; then each block strides over the tiles.
+  uint64_t grid = max_grid ? max_grid : tiles;
+  if (grid > tiles) grid = tiles;
+  if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   sh.grid = static_cast<uint32_t>(grid ? grid : 1);
   return sh;
 }
@@ -477,6 +497,8 @@ bool rows_vpt_supported(uint32_t vpt) { return select_rows(vpt, 1, kPolicyDefaul
 bool rows_shape_supported(uint32_t vpt, uint32_t block) {
   return select_rows(vpt ? vpt : 8, 1, kPolicyStreaming, block ? block : kBlock) != nullptr;
 }
+
+bool batch_vpt_supported(uint32_t vpt) { return select_batch(vpt) != nullptr; }
 
 int batch_blocks_per_sm(uint32_t vpt, uint32_t block) {
   const void *fn = select_batch(vpt);

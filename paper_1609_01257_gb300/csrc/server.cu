@@ -308,9 +308,9 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
     o = *opts;
   }
   if (o.values_per_thread == 0) o.values_per_thread = 8;
-  const uint32_t v = o.values_per_thread;
-  if (v > 32 || (v & (v - 1)))
-    return rngi::fail(err, RNG_EINVAL, "rng_server_create: values_per_thread must be a power of two <= 32");
+  if (!rngi::batch_vpt_supported(o.values_per_thread))
+    return rngi::fail(err, RNG_EINVAL,
+                      "rng_server_create: values_per_thread must be one of 1, 2, 4, 6, 8, 12, 16, 24, 32");
   if (o.max_active == 0 || o.max_steps_in_flight == 0 || o.step_bytes == 0 || o.max_units_per_step == 0 ||
       o.hbm_budget_bytes < kAlign)
     return rngi::fail(err, RNG_EINVAL, "rng_server_create: zero limit in options");

@@ -128,6 +128,19 @@ class Generator:
         """Raw form: ``out_ptr`` is a device address of 8*streams*iterations bytes."""
         C.check(self._lib.rng_generate, self._h, iterations, ctypes.c_void_p(out_ptr), None)
 
+    def generate_ring(self, iterations: int, ring: torch.Tensor) -> torch.Tensor:
+        """Next ``iterations`` rows into ``ring`` (``(R, streams)`` uint64 CUDA
+        tensor), row ``i mod R`` for iteration ``i``; asynchronous."""
+        assert ring.is_cuda and ring.is_contiguous() and ring.element_size() == 8
+        assert ring.numel() % self.streams == 0 and ring.numel() >= self.streams
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(self.device))
+        self.stream.wait_event(ev)
+        C.check(self._lib.rng_generate_ring, self._h, iterations, ctypes.c_void_p(ring.data_ptr()),
+                ring.numel() // self.streams)
+        ring.record_stream(self.stream)
+        return ring
+
     def generate_to_host(self, iterations: int, out=None):
         """Next ``iterations`` rows into host memory (blocks until done).
 

@@ -14,7 +14,7 @@ def test_small_batch_fixed_vpt_all_values():
     streams = [1, 2, 3, 255, 256, 257, 1000, 4099, 70_000]
     iters = [1, 5, 2, 7, 3, 1, 9, 4, 2]
     seeds = [0, 1, 2, 3, 4, 5, 6, 7, 2**64 - 1]
-    for vpt in (1, 2, 8, 32):
+    for vpt in (1, 2, 4, 6, 8, 12, 16, 24, 32):
         b = rng.Batch(streams, iters, seeds, values_per_thread=vpt)
         b.run()
         b.sync()

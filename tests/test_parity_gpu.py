@@ -270,6 +270,24 @@ def test_direct_path_records_one_kernel_and_no_copy():
     assert np.array_equal(host.numpy(), oracle.generate(n, 3, 6))
 
 
+@pytest.mark.parametrize("n,T,R", [(1000, 10, 3), (4096, 7, 7), (4097, 5, 8), (100_001, 9, 2)])
+def test_ring_output_holds_the_last_rows(n, T, R):
+    g = rng.Generator(n, 21)
+    ring = torch.zeros((R, n), dtype=torch.int64, device="cuda").view(torch.uint64)
+    g.generate_ring(T, ring)
+    after = g.generate(2).cpu().numpy()      # the state advanced by T
+    got = ring.cpu().numpy()
+    g.close()
+    want = oracle.generate(n, 21, T + 2)
+    for j in range(R):
+        its = [i for i in range(T) if i % R == j]
+        if its:
+            assert np.array_equal(got[j], want[its[-1]]), (j, its[-1])
+        else:
+            assert (got[j] == 0).all()
+    assert np.array_equal(after, want[T:])
+
+
 def test_live_objects_balance():
     before = rng.live_objects()
     gs = [rng.Generator(100, k) for k in range(3)]
