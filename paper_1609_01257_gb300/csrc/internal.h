@@ -10,6 +10,16 @@
 
 namespace rngi {
 
+constexpr uint32_t kGenBlock = 256;  // threads per block of the generation kernels
+constexpr int kStoreDefault = 0;     // st.global
+constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
+
+// Kernel entry points (kernels.cu); nullptr for shapes that are not compiled.
+const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block);
+const void *checksum_kernel_fn(uint32_t vpt);
+const void *worklist_kernel_fn(uint32_t vpt);
+const void *init_kernel_fn();
+
 // Sets *err (when err != NULL and *err == NULL) and returns `code`.
 int fail(rng_err **err, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 // Wraps a CUDA status: RNG_OK, or RNG_ECUDA / RNG_ENOMEM with the call named.

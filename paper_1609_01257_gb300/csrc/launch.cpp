@@ -1,0 +1,167 @@
+// Host-side launch code of the generation kernels: shape selection (values
+// per thread, store width, grid) and the launches themselves.  The kernels
+// are in kernels.cu; this file holds no device code.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace rngi {
+namespace {
+
+int occupancy(const void *fn, uint32_t block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, static_cast<int>(block), 0) !=
+          cudaSuccess ||
+      n < 1)
+    n = 1;
+  return n;
+}
+
+
+}  // namespace
+
+int device_sm_count(int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+    sms = 1;
+  return sms;
+}
+
+// Values per thread for 256-thread blocks, from sweeps of the row kernel on
+// GB300 (152 SMs) writing 16-32 GiB per point with one tile per block: 24
+// streams per thread (one 48 KiB run per block and row, one resident block
+// per SM) was fastest from 2^22 to 2^26 streams and 12 around 2^21.  Below
+// that, the fastest shapes made about 128 tiles (one long-running block on
+// most SMs): 32 at 2^20, 8 at 2^18, 2 at 2^16.
+uint32_t default_vpt(uint64_t streams, int sms) {
+  const uint64_t M = uint64_t(1) << 20;
+  if (streams >= 7 * M / 2) return 24;
+  if (streams >= 3 * M / 2) return 12;
+  (void)sms;
+  const uint64_t v = streams / (uint64_t(kGenBlock) * 128);
+  for (uint32_t c : {32u, 16u, 8u, 4u, 2u})
+    if (v >= c) return c;
+  return 1;
+}
+
+LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid,
+                       uint32_t width, int policy) {
+  LaunchShape sh;
+  sh.block = block ? block : kGenBlock;
+  const int sms = device_sm_count(device);
+  if (vpt == 0) vpt = sh.block == kGenBlock ? default_vpt(streams, sms) : 8;
+  sh.vpt = vpt;
+  // One 8-byte store per value measured fastest once a thread holds six or
+  // more streams (see the shape sweep in the design notes); below that the
+  // widest store the alignment allows.
+  sh.width = width ? width : (vpt >= 6 ? 1 : 4);
+  // Occupancy of the variant that will run (policy and store width change
+  // the register count).
+  const void *fn = rows_kernel_fn(vpt, static_cast<int>(sh.width), sh.block == kGenBlock ? policy : kStoreStreaming, sh.block);
+  if (!fn) {
+    sh.grid = 0;
+    return sh;
+  }
+  const uint64_t tiles = (streams + static_cast<uint64_t>(sh.block) * vpt - 1) /
+                         (static_cast<uint64_t>(sh.block) * vpt);
+  // One block per tile by default: the hardware hands tiles out in order as
+  // blocks finish, which measured ~10% faster than a persistent grid-stride
+  // loop (tiles running at the same time stay adjacent in memory).  max_grid
+  // asks for fewer blocks; then each block strides over the tiles.
+  uint64_t grid = max_grid ? max_grid : tiles;
+  if (grid > tiles) grid = tiles;
+  if (grid > 0x7fffffffull) grid = 0x7fffffffull;
+  sh.grid = static_cast<uint32_t>(grid ? grid : 1);
+  return sh;
+}
+
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st) {
+  // Widest store the output's alignment allows: every row must start on an
+  // 8*W-byte boundary (pitch a multiple of W, base aligned to 8*W bytes).
+  int width = 1;
+  const uintptr_t base = reinterpret_cast<uintptr_t>(a.out);
+  for (int w : {4, 2})
+    if (a.out && a.pitch % w == 0 && base % (8 * w) == 0) {
+      width = w;
+      break;
+    }
+  if (width > static_cast<int>(sh.width)) width = static_cast<int>(sh.width);
+  const void *fn = rows_kernel_fn(sh.vpt, width, store_policy, sh.block);
+  if (!fn) return cudaErrorInvalidValue;
+  RowsLaunch args = a;
+  void *params[] = {&args};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
+                        cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t blocks_needed = (n + 255) / 256;
+  const uint64_t cap = static_cast<uint64_t>(device_sm_count(dev)) * 8;
+  const unsigned grid = static_cast<unsigned>(blocks_needed < cap ? blocks_needed : cap);
+  void *params[] = {&state, &n, &id_base, &key};
+  cudaError_t e = cudaLaunchKernel(init_kernel_fn(), dim3(grid ? grid : 1), dim3(256), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,
+                            cudaStream_t st) {
+  const uint64_t span = a.s_end - a.s_begin;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int sms = device_sm_count(dev);
+  if (vpt == 0) {
+    // Enough values per thread to amortise the per-row reductions, while
+    // keeping at least one tile per resident block slot.
+    vpt = 1;
+    for (uint32_t v = 16; v >= 2; v /= 2)
+      if (span / (uint64_t(kGenBlock) * v) >= uint64_t(sms) * 4) {
+        vpt = v;
+        break;
+      }
+  }
+  const void *fn = checksum_kernel_fn(vpt);
+  if (!fn) return cudaErrorInvalidValue;
+  const uint64_t tiles = (span + uint64_t(kGenBlock) * vpt - 1) / (uint64_t(kGenBlock) * vpt);
+  const uint64_t resident = uint64_t(sms) * occupancy(fn, kGenBlock);
+  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(tiles, resident)));
+  RowsLaunch args = a;
+  unsigned long long *rx = reinterpret_cast<unsigned long long *>(row_xor);
+  unsigned long long *rs = reinterpret_cast<unsigned long long *>(row_sum);
+  void *params[] = {&args, &rx, &rs};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kGenBlock), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+bool rows_vpt_supported(uint32_t vpt) { return rows_kernel_fn(vpt, 1, kStoreDefault, kGenBlock) != nullptr; }
+bool rows_shape_supported(uint32_t vpt, uint32_t block) {
+  return rows_kernel_fn(vpt ? vpt : 8, 1, kStoreStreaming, block ? block : kGenBlock) != nullptr;
+}
+
+bool batch_vpt_supported(uint32_t vpt) { return worklist_kernel_fn(vpt) != nullptr; }
+
+int batch_blocks_per_sm(uint32_t vpt, uint32_t block) {
+  const void *fn = worklist_kernel_fn(vpt);
+  return fn ? occupancy(fn, block) : 0;
+}
+
+cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint32_t n_units,
+                         uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
+                         cudaStream_t st) {
+  const void *fn = worklist_kernel_fn(vpt);
+  if (!fn || block != kGenBlock) return cudaErrorInvalidValue;
+  void *params[] = {&inst, &units, &n_units, &counter};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+}  // namespace rngi
