@@ -508,7 +508,7 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0,
                     help="iterations in the CPU-baseline sample (0 = the whole workload)")
-    ap.add_argument("--reference-rows", type=int, default=16, help="iterations per reference step")
+    ap.add_argument("--reference-rows", type=int, default=128, help="iterations per reference step")
     ap.add_argument("--iterations", type=int, default=0,
                     help="override the workload's iteration count (profiling captures of a smaller case)")
     args = ap.parse_args(argv)

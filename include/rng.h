@@ -191,6 +191,16 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink,
 int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev,
                           uint64_t *row_sum_dev, rng_err **err);
 
+/* Jump-ahead: advances every stream by `iterations` iterations without
+ * producing them (position p += iterations, modulo 2^64).  The update of
+ * Listing S5 is linear over GF(2), so k iterations are one multiplication by
+ * the k-th power of its 64x64 bit matrix, computed on the host by repeated
+ * squaring and applied by one kernel (64 conditional XORs per stream).  The
+ * update has period 2^64 - 1: skipping that many returns every stream to its
+ * current state.  For resuming a run, checkpoints, and splitting a run by
+ * iterations across callers.  Ordered on the compute stream. */
+int rng_skip(rng_gen *g, uint64_t iterations, rng_err **err);
+
 /* Current position p (next iteration to be emitted) and stream count. */
 int rng_position(const rng_gen *g, uint64_t *position);
 int rng_streams(const rng_gen *g, uint64_t *streams);
@@ -388,6 +398,23 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
  * or the scheduler's error if it has failed. */
 int rng_server_submit(rng_server *s, uint64_t seed, uint64_t streams, uint64_t iterations,
                       uint64_t *ticket, rng_err **err);
+/* Request flags. */
+enum {
+    RNG_REQ_KEEP_STATE = 1  /* keep the final states resident on the device
+                               after completion, for a continuation */
+};
+/* Like rng_server_submit, with flags and continuation: when
+ * continue_ticket != 0 it names a request submitted with
+ * RNG_REQ_KEEP_STATE (and not continued before); the new request continues
+ * that generator -- same seed and streams (the seed and streams arguments
+ * are ignored), iterations starting where it stopped -- from its states
+ * kept on the device, so nothing is recomputed or copied.  The continuation
+ * is admitted once its parent has completed.  Kept states are freed when the
+ * continuation takes them over, or when a request that nobody continues is
+ * released. */
+int rng_server_submit_ex(rng_server *s, uint64_t seed, uint64_t streams, uint64_t iterations,
+                         uint32_t flags, uint64_t continue_ticket, uint64_t *ticket,
+                         rng_err **err);
 /* Returns up to `max` completed requests not returned before: ticket,
  * device address of its output (8*streams*iterations bytes, owned by the
  * server until released) and latency in seconds (submission to completion

@@ -96,6 +96,7 @@ SIGNATURES = {
     "rng_generate_sink": ([c_vp, c_u64, SINK_FN, c_vp, P_err], c_int),
     "rng_generate_ring": ([c_vp, c_u64, c_vp, c_u64, P_err], c_int),
     "rng_generate_checksum": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
+    "rng_skip": ([c_vp, c_u64, P_err], c_int),
     "rng_position": ([c_vp, P_u64], c_int),
     "rng_streams": ([c_vp, P_u64], c_int),
     "rng_get_state": ([c_vp, c_vp, P_err], c_int),
@@ -137,6 +138,7 @@ SIGNATURES = {
     "rng_server_opts_default": ([ctypes.POINTER(RngServerOpts)], None),
     "rng_server_create": ([ctypes.POINTER(RngServerOpts), ctypes.POINTER(c_vp), P_err], c_int),
     "rng_server_submit": ([c_vp, c_u64, c_u64, c_u64, P_u64, P_err], c_int),
+    "rng_server_submit_ex": ([c_vp, c_u64, c_u64, c_u64, c_u32, c_u64, P_u64, P_err], c_int),
     "rng_server_poll": ([c_vp, c_u32, P_u64, ctypes.POINTER(c_vp), ctypes.POINTER(c_dbl),
                          ctypes.POINTER(c_u32), c_u32, P_err], c_int),
     "rng_server_read": ([c_vp, c_u64, c_u64, c_u64, c_vp, P_err], c_int),

@@ -672,6 +672,21 @@ int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev
   return RNG_OK;
 }
 
+int rng_skip(rng_gen *g, uint64_t iterations, rng_err **err) {
+  int rc = check_gen(g, err, "rng_skip");
+  if (rc) return rc;
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_skip: generator not initialised (call rng_init)");
+  if (iterations == 0) return RNG_OK;
+  long op = op_begin(g, "SKIP_KERNEL", kQueueMain, g->compute);
+  cudaError_t st = rngi::launch_jump(g->d_state, g->n, g->g0, g->key, !g->materialized, iterations, g->compute);
+  op_end(g, op, g->compute);
+  rc = rngi::cuda_fail(err, st, "jump kernel launch");
+  if (rc) return rc;
+  g->materialized = true;
+  g->pos += iterations;  // wraps modulo 2^64 like the period of the update
+  return RNG_OK;
+}
+
 int rng_position(const rng_gen *g, uint64_t *position) {
   if (!g || !position) return RNG_EINVAL;
   *position = g->pos;

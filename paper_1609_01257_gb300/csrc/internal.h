@@ -19,6 +19,7 @@ const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block);
 const void *checksum_kernel_fn(uint32_t vpt);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *init_kernel_fn();
+const void *jump_kernel_fn();
 
 // Sets *err (when err != NULL and *err == NULL) and returns `code`.
 int fail(rng_err **err, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -67,6 +68,10 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
 cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st);
 cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
                         cudaStream_t st);
+// state[s] := M^k applied to the state of stream s (from the hash when
+// from_hash), where M is the update's matrix over GF(2).
+cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key, int from_hash,
+                        uint64_t k, cudaStream_t st);
 // Generate-and-checksum launch; vpt = 0 picks values per thread (a power of
 // two up to 64 otherwise).
 cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,

@@ -161,6 +161,26 @@ __global__ void init_kernel(uint64_t *__restrict__ state, uint64_t n, uint64_t i
     state[s] = prng::initial_state(id_base + s, key);
 }
 
+// Jump-ahead: every state is multiplied by a 64x64 matrix over GF(2) given
+// by its columns (col[j] = image of bit j), i.e. advanced by the number of
+// iterations the matrix stands for.  The update is linear over GF(2), so k
+// iterations are the k-th power of its matrix.
+struct JumpMatrix {
+  uint64_t col[64];
+};
+
+__global__ void jump_kernel(uint64_t *__restrict__ state, uint64_t n, uint64_t id_base, uint32_t key,
+                            int from_hash, const JumpMatrix m) {
+  for (uint64_t s = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; s < n;
+       s += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint64_t v = from_hash ? prng::initial_state(id_base + s, key) : state[s];
+    uint64_t acc = 0;
+#pragma unroll 16
+    for (int j = 0; j < 64; ++j) acc ^= m.col[j] & (0ull - ((v >> j) & 1ull));
+    state[s] = acc;
+  }
+}
+
 // 64-bit XOR and wrapping sum across a warp with 32-bit reductions: the sum
 // is split into two 16-bit low parts (no carry can be lost over 32 lanes)
 // and the high word, whose sum only matters modulo 2^32.
@@ -372,5 +392,6 @@ const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block) 
 const void *checksum_kernel_fn(uint32_t vpt) { return select_checksum(vpt); }
 const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }
 const void *init_kernel_fn() { return reinterpret_cast<const void *>(&init_kernel); }
+const void *jump_kernel_fn() { return reinterpret_cast<const void *>(&jump_kernel); }
 
 }  // namespace rngi

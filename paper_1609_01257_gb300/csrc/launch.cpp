@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "prng_math.cuh"
 
 namespace rngi {
 namespace {
@@ -107,6 +108,58 @@ cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t 
   const unsigned grid = static_cast<unsigned>(blocks_needed < cap ? blocks_needed : cap);
   void *params[] = {&state, &n, &id_base, &key};
   cudaError_t e = cudaLaunchKernel(init_kernel_fn(), dim3(grid ? grid : 1), dim3(256), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+namespace {
+
+// 64x64 matrices over GF(2) as 64 column words (column j = image of bit j).
+struct Gf2 {
+  uint64_t col[64];
+};
+
+uint64_t gf2_apply(const Gf2 &m, uint64_t v) {
+  uint64_t acc = 0;
+  for (int j = 0; j < 64; ++j)
+    if ((v >> j) & 1) acc ^= m.col[j];
+  return acc;
+}
+
+Gf2 gf2_mul(const Gf2 &a, const Gf2 &b) {  // a * b: apply b first
+  Gf2 r;
+  for (int j = 0; j < 64; ++j) r.col[j] = gf2_apply(a, b.col[j]);
+  return r;
+}
+
+// M^k for the xorshift update: columns of M are the update of each unit
+// vector; the power by repeated squaring.
+Gf2 update_power(uint64_t k) {
+  Gf2 base, result;
+  for (int j = 0; j < 64; ++j) {
+    base.col[j] = prng::xorshift_update(uint64_t(1) << j);
+    result.col[j] = uint64_t(1) << j;
+  }
+  while (k) {
+    if (k & 1) result = gf2_mul(base, result);
+    base = gf2_mul(base, base);
+    k >>= 1;
+  }
+  return result;
+}
+
+}  // namespace
+
+cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key, int from_hash,
+                        uint64_t k, cudaStream_t st) {
+  Gf2 m = update_power(k);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t blocks_needed = (n + 255) / 256;
+  const uint64_t cap = static_cast<uint64_t>(device_sm_count(dev)) * 8;
+  const unsigned grid = static_cast<unsigned>(blocks_needed < cap ? blocks_needed : cap);
+  void *params[] = {&state, &n, &id_base, &key, &from_hash, &m};
+  cudaError_t e = cudaLaunchKernel(jump_kernel_fn(), dim3(grid ? grid : 1), dim3(256), params, 0, st);
   if (e == cudaSuccess) count_launch();
   return e;
 }

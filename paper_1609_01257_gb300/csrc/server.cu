@@ -43,6 +43,13 @@ struct Request {
   Clock::time_point t_submit;
   double latency = 0.0;
   bool done = false;
+  bool released = false;      // output returned; kept only for its state
+  bool keep_state = false;    // final states stay resident for a continuation
+  bool has_state = false;     // state_off/state_bytes hold an arena block
+  bool state_is_hash = true;  // first chunk starts from the id hash
+  uint64_t first_iteration = 0;
+  uint64_t parent = 0;        // ticket continued from (0: fresh generator)
+  uint64_t child = 0;         // ticket continuing this one
 };
 
 struct TableSlot {
@@ -170,8 +177,8 @@ struct rng_server {
       in.rows = rows;
       in.key = r->key;
       in.vec = (r->streams % 2 == 0) ? 1u : 0u;  // arena blocks are 256-byte aligned
-      in.from_hash = r->issued == 0 ? 1u : 0u;
-      in.write_state = (r->issued + rows < r->iters) ? 1u : 0u;
+      in.from_hash = (r->issued == 0 && r->state_is_hash) ? 1u : 0u;
+      in.write_state = (r->issued + rows < r->iters || r->keep_state) ? 1u : 0u;
       for (uint64_t s0 = 0; s0 < r->streams; s0 += tile)
         ts.h_units[n_units++] = {n_inst, static_cast<uint32_t>(std::min(tile, r->streams - s0)), s0};
       ++n_inst;
@@ -220,8 +227,10 @@ struct rng_server {
         Request *r = tickets[t];
         r->latency = std::chrono::duration<double>(now - r->t_submit).count();
         r->done = true;
-        arena.release(r->state_off, r->state_bytes);
-        r->state_bytes = 0;
+        if (!r->keep_state && r->has_state) {
+          arena.release(r->state_off, r->state_bytes);
+          r->has_state = false;
+        }
         active.erase(std::find(active.begin(), active.end(), r));
         done_q.push_back(t);
         st.completed++;
@@ -232,17 +241,34 @@ struct rng_server {
     }
   }
 
+  // A continuation can start once its parent has finished: it takes over the
+  // parent's resident states instead of hashing the ids.
   void admit_locked() {
     while (!pending.empty() && active.size() < opts.max_active) {
       Request *r = pending.front();
-      uint64_t out_off, state_off;
+      Request *parent = r->parent ? tickets[r->parent] : nullptr;
+      if (parent && !parent->done) return;  // arrival order is kept
+      uint64_t out_off, state_off = 0;
       if (!arena.alloc(r->out_bytes, &out_off)) return;
-      if (!arena.alloc(r->state_bytes, &state_off)) {
-        arena.release(out_off, r->out_bytes);
-        return;
+      if (parent) {
+        r->state_off = parent->state_off;
+        r->state_bytes = parent->state_bytes;
+        r->has_state = true;
+        r->state_is_hash = false;
+        parent->has_state = false;
+        if (parent->released) {
+          tickets.erase(parent->ticket);
+          delete parent;
+        }
+      } else {
+        if (!arena.alloc(r->state_bytes, &state_off)) {
+          arena.release(out_off, r->out_bytes);
+          return;
+        }
+        r->state_off = state_off;
+        r->has_state = true;
       }
       r->out_off = out_off;
-      r->state_off = state_off;
       pending.pop_front();
       active.push_back(r);
       st.peak_active = std::max<uint64_t>(st.peak_active, active.size());
@@ -355,9 +381,23 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
   return RNG_OK;
 }
 
-int rng_server_submit(rng_server *s, uint64_t seed, uint64_t streams, uint64_t iterations, uint64_t *ticket,
-                      rng_err **err) {
+int rng_server_submit_ex(rng_server *s, uint64_t seed, uint64_t streams, uint64_t iterations, uint32_t flags,
+                         uint64_t continue_ticket, uint64_t *ticket, rng_err **err) {
   if (!s || !ticket) return rngi::fail(err, RNG_EINVAL, "rng_server_submit: NULL argument");
+  if (flags & ~uint32_t(RNG_REQ_KEEP_STATE))
+    return rngi::fail(err, RNG_EINVAL, "rng_server_submit: unknown flags 0x%x", flags);
+  std::lock_guard<std::mutex> lk(s->mu);
+  Request *parent = nullptr;
+  if (continue_ticket) {
+    auto it = s->tickets.find(continue_ticket);
+    if (it == s->tickets.end() || !it->second->keep_state || it->second->child)
+      return rngi::fail(err, RNG_ESTATE,
+                        "rng_server_submit: ticket %llu is not a request kept for continuation (or already continued)",
+                        (unsigned long long)continue_ticket);
+    parent = it->second;
+    seed = parent->seed;
+    streams = parent->streams;
+  }
   if (streams == 0 || streams > (uint64_t(1) << 32) || iterations == 0)
     return rngi::fail(err, RNG_EINVAL, "rng_server_submit: streams must be in [1, 2^32] and iterations >= 1");
   if (iterations > (~uint64_t(0) / 8) / streams - 1)
@@ -365,27 +405,30 @@ int rng_server_submit(rng_server *s, uint64_t seed, uint64_t streams, uint64_t i
   const uint64_t tile = uint64_t(kBlock) * s->opts.values_per_thread;
   if ((streams + tile - 1) / tile > s->opts.max_units_per_step)
     return rngi::fail(err, RNG_EINVAL, "rng_server_submit: request wider than one step's work table");
+  if (s->fatal != RNG_OK)
+    return rngi::fail(err, s->fatal, "rng_server_submit: server failed: %s", s->fatal_msg.c_str());
+  const uint64_t out_bytes = 8 * streams * iterations, state_bytes = 8 * streams;
+  const uint64_t need = (out_bytes + kAlign - 1) / kAlign * kAlign + (state_bytes + kAlign - 1) / kAlign * kAlign;
+  if (need > s->opts.hbm_budget_bytes) {
+    s->st.rejected++;
+    return rngi::fail(err, RNG_EBUDGET, "rng_server_submit: request needs %llu bytes, budget is %llu",
+                      (unsigned long long)need, (unsigned long long)s->opts.hbm_budget_bytes);
+  }
   Request *r = new (std::nothrow) Request();
   if (!r) return rngi::fail(err, RNG_ENOMEM, "rng_server_submit: host allocation failed");
   r->seed = seed;
   r->streams = streams;
   r->iters = iterations;
   r->key = prng::seed_key(seed);
-  r->out_bytes = 8 * streams * iterations;
-  r->state_bytes = 8 * streams;
-  const uint64_t need = (r->out_bytes + kAlign - 1) / kAlign * kAlign + (r->state_bytes + kAlign - 1) / kAlign * kAlign;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (s->fatal != RNG_OK) {
-    delete r;
-    return rngi::fail(err, s->fatal, "rng_server_submit: server failed: %s", s->fatal_msg.c_str());
-  }
-  if (need > s->opts.hbm_budget_bytes) {
-    delete r;
-    s->st.rejected++;
-    return rngi::fail(err, RNG_EBUDGET, "rng_server_submit: request needs %llu bytes, budget is %llu",
-                      (unsigned long long)need, (unsigned long long)s->opts.hbm_budget_bytes);
-  }
+  r->out_bytes = out_bytes;
+  r->state_bytes = state_bytes;
+  r->keep_state = (flags & RNG_REQ_KEEP_STATE) != 0;
   r->ticket = s->next_ticket++;
+  if (parent) {
+    r->parent = parent->ticket;
+    r->first_iteration = parent->first_iteration + parent->iters;
+    parent->child = r->ticket;
+  }
   r->t_submit = Clock::now();
   s->tickets[r->ticket] = r;
   s->pending.push_back(r);
@@ -393,6 +436,11 @@ int rng_server_submit(rng_server *s, uint64_t seed, uint64_t streams, uint64_t i
   *ticket = r->ticket;
   s->cv_sched.notify_one();
   return RNG_OK;
+}
+
+int rng_server_submit(rng_server *s, uint64_t seed, uint64_t streams, uint64_t iterations, uint64_t *ticket,
+                      rng_err **err) {
+  return rng_server_submit_ex(s, seed, streams, iterations, 0, 0, ticket, err);
 }
 
 int rng_server_poll(rng_server *s, uint32_t max, uint64_t *tickets, uint64_t **outs, double *latency_s,
@@ -424,8 +472,8 @@ int rng_server_read(rng_server *s, uint64_t ticket, uint64_t first, uint64_t cou
   {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->tickets.find(ticket);
-    if (it == s->tickets.end() || !it->second->done)
-      return rngi::fail(err, RNG_ESTATE, "rng_server_read: ticket %llu is not a completed request",
+    if (it == s->tickets.end() || !it->second->done || it->second->released)
+      return rngi::fail(err, RNG_ESTATE, "rng_server_read: ticket %llu is not a completed, unreleased request",
                         (unsigned long long)ticket);
     Request *r = it->second;
     if (first > r->streams * r->iters || count > r->streams * r->iters - first)
@@ -440,14 +488,23 @@ int rng_server_release(rng_server *s, uint64_t ticket, rng_err **err) {
   if (!s) return rngi::fail(err, RNG_EINVAL, "rng_server_release: NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->tickets.find(ticket);
-  if (it == s->tickets.end() || !it->second->done)
-    return rngi::fail(err, RNG_ESTATE, "rng_server_release: ticket %llu is not a completed request",
+  if (it == s->tickets.end() || !it->second->done || it->second->released)
+    return rngi::fail(err, RNG_ESTATE, "rng_server_release: ticket %llu is not a completed, unreleased request",
                       (unsigned long long)ticket);
   Request *r = it->second;
+  if (r->released)
+    return rngi::fail(err, RNG_ESTATE, "rng_server_release: ticket %llu already released", (unsigned long long)ticket);
   s->arena.release(r->out_off, r->out_bytes);
-  s->tickets.erase(it);
-  delete r;
+  r->released = true;
   s->st.released++;
+  if (r->has_state && !r->child) {  // kept states nobody continues: free them too
+    s->arena.release(r->state_off, r->state_bytes);
+    r->has_state = false;
+  }
+  if (!r->has_state) {
+    s->tickets.erase(it);
+    delete r;
+  }
   s->cv_sched.notify_one();
   return RNG_OK;
 }

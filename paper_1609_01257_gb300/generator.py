@@ -91,6 +91,10 @@ class Generator:
     def init(self):
         C.check(self._lib.rng_init, self._h)
 
+    def skip(self, iterations: int):
+        """Advance every stream by ``iterations`` (jump-ahead over GF(2))."""
+        C.check(self._lib.rng_skip, self._h, iterations & ((1 << 64) - 1))
+
     @property
     def position(self) -> int:
         p = ctypes.c_uint64()

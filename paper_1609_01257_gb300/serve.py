@@ -49,6 +49,14 @@ class Server:
                 ctypes.byref(t))
         return t.value
 
+    def submit_ex(self, seed: int, streams: int, iterations: int, *, keep_state: bool = False,
+                  continue_ticket: int = 0) -> int:
+        """Submit with state retention and/or as the continuation of a kept request."""
+        t = ctypes.c_uint64()
+        C.check(self._lib.rng_server_submit_ex, self._h, seed & ((1 << 64) - 1), streams, iterations,
+                1 if keep_state else 0, continue_ticket, ctypes.byref(t))
+        return t.value
+
     def poll(self, max_items: int = 256, timeout_ms: int = 50):
         """Completed requests: list of (ticket, device address, latency seconds)."""
         tk = (ctypes.c_uint64 * max_items)()

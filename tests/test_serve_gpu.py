@@ -113,6 +113,37 @@ def test_budget_admission_and_release():
             srv.release(t1)                     # already released
 
 
+def test_continuations_use_resident_states():
+    n, seed = 5000, 31
+    with rng.Server(hbm_budget_bytes=1 << 30, step_bytes=1 << 20) as srv:
+        a = srv.submit_ex(seed, n, 7, keep_state=True)
+        b = srv.submit_ex(0, 0, 5, keep_state=True, continue_ticket=a)  # queued behind its parent
+        c = srv.submit_ex(0, 0, 3, continue_ticket=b)
+        _collect(srv, 3)
+        want = oracle.generate(n, seed, 15)
+        assert np.array_equal(_full(srv, a, n, 7), want[:7])
+        srv.release(a)
+        assert np.array_equal(_full(srv, b, n, 5), want[7:12])
+        assert np.array_equal(_full(srv, c, n, 3), want[12:15])
+        with pytest.raises(rng.RngError) as e:
+            srv.submit_ex(0, 0, 1, continue_ticket=c)  # c did not keep its states
+        assert e.value.code == C.RNG_ESTATE
+        with pytest.raises(rng.RngError):
+            srv.submit_ex(0, 0, 1, continue_ticket=a)  # a was continued already
+        srv.release(b)
+        srv.release(c)
+        assert srv.stats()["bytes_in_use"] == 0
+
+
+def test_kept_state_freed_on_release_without_continuation():
+    with rng.Server(hbm_budget_bytes=1 << 30) as srv:
+        t = srv.submit_ex(4, 4096, 3, keep_state=True)
+        _collect(srv, 1)
+        assert srv.stats()["bytes_in_use"] > 8 * 4096 * 3
+        srv.release(t)
+        assert srv.stats()["bytes_in_use"] == 0
+
+
 def test_invalid_requests():
     with rng.Server(hbm_budget_bytes=1 << 20) as srv:
         for args in [(1, 0, 5), (1, 5, 0), (1, (1 << 32) + 1, 1)]:
