@@ -381,7 +381,8 @@ def run_served(args):
 
     reqs = workloads.served_requests(duration_s=args.duration)
     offered = sum(r.nbytes for r in reqs)
-    with rng.Server(hbm_budget_bytes=64 << 30) as srv:
+    with rng.Server(hbm_budget_bytes=64 << 30, step_bytes=args.step_bytes,
+                    max_steps_in_flight=args.steps_in_flight, values_per_thread=args.server_vpt) as srv:
         warm = workloads.served_requests(duration_s=0.5, seed_start=5, arrival_start=6, size_start=7)
         rng.run_load(srv, warm)
         res = rng.run_load(srv, reqs)
@@ -393,6 +394,8 @@ def run_served(args):
                 "aggregate_GBps": res.bytes / res.wall_s / 1e9, "offered_GBps": offered / args.duration / 1e9,
                 "wall_s": res.wall_s, "worst_submit_lag_ms": res.submit_lag_s * 1e3,
                 "steps": st["steps"], "peak_active": st["peak_active"],
+                "server": {"step_bytes": args.step_bytes, "steps_in_flight": args.steps_in_flight,
+                           "values_per_thread": args.server_vpt},
                 "peak_bytes_in_use": st["peak_bytes_in_use"]})
     return 0
 
@@ -502,6 +505,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum"], default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
+    ap.add_argument("--step-bytes", type=int, default=512 << 20, help="served: output bytes per step")
+    ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
+    ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")

@@ -182,6 +182,15 @@ typedef int (*rng_sink_fn)(void *user, uint64_t first_iteration, uint64_t rows,
 int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink,
                       void *user, rng_err **err);
 
+/* The paper's program output (Section 5: raw binary values to stdout, for
+ * piping to a consumer such as a statistical test suite): streams
+ * `iterations` rows, in order, to the file descriptor `fd` (e.g. 1 for
+ * stdout) as native-endian uint64 values, through the double buffer and the
+ * pinned staging slots, a library thread writing one slot while the next is
+ * filled (the host-side dual buffer the paper names as an improvement).
+ * Blocks until everything is written; RNG_ESINK if a write fails. */
+int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err);
+
 /* Generate-and-checksum mode: advances the streams through iterations
  * p .. p+iterations-1 without storing the values and writes, for each
  * iteration, the XOR (row_xor_dev[it-p]) and the wrapping sum modulo 2^64

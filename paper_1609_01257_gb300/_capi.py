@@ -95,6 +95,7 @@ SIGNATURES = {
     "rng_generate": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
     "rng_generate_sink": ([c_vp, c_u64, SINK_FN, c_vp, P_err], c_int),
     "rng_generate_ring": ([c_vp, c_u64, c_vp, c_u64, P_err], c_int),
+    "rng_generate_fd": ([c_vp, c_u64, c_int, P_err], c_int),
     "rng_generate_checksum": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
     "rng_skip": ([c_vp, c_u64, P_err], c_int),
     "rng_position": ([c_vp, P_u64], c_int),

@@ -10,7 +10,9 @@
 // stream (`copied[b]` and `produced[b]`), so neither host thread blocks on
 // the device between launches.
 #include <cuda_runtime.h>
+#include <errno.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <chrono>
 #include <condition_variable>
@@ -635,6 +637,31 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink, void *u
   rc = size_ok(g->n, iterations, err);
   if (rc) return rc;
   return double_buffer_host(g, iterations, nullptr, sink, user, err);
+}
+
+// Sink of rng_generate_fd: writes each chunk's bytes to the descriptor,
+// retrying short writes and interrupted calls.
+static int fd_sink(void *user, uint64_t, uint64_t rows, uint64_t, uint64_t n_streams, uint64_t,
+                   const uint64_t *values) {
+  const int fd = *static_cast<const int *>(user);
+  const char *p = reinterpret_cast<const char *>(values);
+  size_t left = rows * n_streams * 8;
+  while (left) {
+    const ssize_t w = write(fd, p, left);
+    if (w < 0) {
+      if (errno == EINTR) continue;
+      return errno ? errno : 1;
+    }
+    p += w;
+    left -= static_cast<size_t>(w);
+  }
+  return 0;
+}
+
+int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err) {
+  if (fd < 0) return rngi::fail(err, RNG_EINVAL, "rng_generate_fd: bad file descriptor %d", fd);
+  int user = fd;
+  return rng_generate_sink(g, iterations, fd_sink, &user, err);
 }
 
 int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev, uint64_t *row_sum_dev,

@@ -189,6 +189,10 @@ class Generator:
                 raise failure[0]
             raise
 
+    def generate_fd(self, iterations: int, fd: int):
+        """Stream ``iterations`` rows as raw uint64 values to file descriptor ``fd``."""
+        C.check(self._lib.rng_generate_fd, self._h, iterations, fd)
+
     def generate_checksum(self, iterations: int, row_xor: Optional[torch.Tensor] = None,
                           row_sum: Optional[torch.Tensor] = None):
         """Per-iteration XOR and wrapping sum over all streams, without

@@ -76,9 +76,9 @@ def test_request_spanning_many_steps_continues_from_resident_state():
 def test_small_requests_overtake_a_large_one():
     # Continuous batching: requests that arrive while a large one is on the
     # GPU are admitted and finish before it does.
-    with rng.Server(hbm_budget_bytes=9 << 30, step_bytes=16 << 20) as srv:
-        big = srv.submit(1, 1 << 22, 256)        # 8 GiB of output over many steps
-        time.sleep(0.002)
+    # The large request (32 GiB) needs at least 1024 steps of one 32 MiB row.
+    with rng.Server(hbm_budget_bytes=40 << 30, step_bytes=16 << 20) as srv:
+        big = srv.submit(1, 1 << 22, 1024)
         small = [srv.submit(100 + k, 1024, 4) for k in range(10)]
         order = []
         t_end = time.time() + 60
@@ -88,9 +88,9 @@ def test_small_requests_overtake_a_large_one():
         assert order[-1] == big, order
         for k, t in enumerate(small):
             assert np.array_equal(_full(srv, t, 1024, 4), oracle.generate(1024, 100 + k, 4))
-        got = srv.read(big, (255 << 22) + 12345, 3)
+        got = srv.read(big, (1023 << 22) + 12345, 3)
         for j in range(3):
-            assert int(got[j]) == oracle.value(12345 + j, 1, 255)
+            assert int(got[j]) == oracle.value(12345 + j, 1, 1023)
 
 
 def test_budget_admission_and_release():
