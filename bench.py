@@ -442,6 +442,35 @@ def run_checksum(args, wl):
     return 0
 
 
+def run_queue_chart(args):
+    """The run the paper charts (Section 4.2, queue utilisation figure): 2^24
+    values per iteration, 8 iterations, the double buffer with one 128 MiB row
+    per device buffer; prints every profiled event (queue, start, end, name)."""
+    import tempfile
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    n, T = 1 << 24, 8
+    host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
+    g = rng.Generator(n, 0, device_buffer_bytes=8 * n, host_path=1, init=False)
+    for _ in range(args.warmup):
+        g.init()
+        g.generate_to_host(T, host)
+    g.init()
+    g.profile_reset()
+    g.generate_to_host(T, host)
+    with tempfile.NamedTemporaryFile("r", suffix=".tsv") as f:
+        g.profile_export(f.name)
+        events = [line.rstrip("\n").split("\t") for line in open(f.name)]
+    summary = g.profile_summary()
+    g.close()
+    _json_line({"workload": "queue chart: 2^24 values per iteration x 8 iterations, double buffer",
+                "events": [[q, int(float(a)), int(float(b)), nm] for q, a, b, nm in events],
+                "summary": summary})
+    return 0
+
+
 def run_sweep(args):
     """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread.
     Output goes to a ring of two 2 GiB device buffers: each launch writes the
@@ -503,9 +532,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum"], default="streaming")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart"], default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
-    ap.add_argument("--step-bytes", type=int, default=512 << 20, help="served: output bytes per step")
+    ap.add_argument("--step-bytes", type=int, default=2 << 30, help="served: output bytes per step")
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
@@ -525,6 +554,8 @@ def main(argv=None):
         return run_served(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "queue-chart":
+        return run_queue_chart(args)
     wl = dict(WORKLOADS["streaming" if args.workload == "checksum" else args.workload])
     if args.iterations:
         wl["iterations"] = args.iterations

@@ -116,7 +116,7 @@ void rng_opts_default(rng_opts *opts);
 /* ------------------------------------------------------------------ */
 /* Generator (Section 5: init kernel, rng kernel, device->host reads)  */
 /* ------------------------------------------------------------------ */
-typedef struct rng_gen rng_gen;
+typedef struct rng_gen rng_gen;  /* use one generator from one host thread at a time */
 
 /* Creates a generator of `streams` streams (1 <= streams <= 2^32; ids
  * are reduced to 32 bits before hashing, as in Listing S4) with run seed
@@ -151,7 +151,10 @@ int rng_init(rng_gen *g, rng_err **err);
  *    rng_opts.host_path).  Blocks until every value is in out_host (the
  *    paper's blocking read).
  * iterations == 0 is a no-op.  Errors: RNG_EINVAL (both or neither output,
- * size overflow), RNG_ESTATE (not initialised), RNG_ECUDA. */
+ * size overflow), RNG_ESTATE (not initialised), RNG_ENOMEM (device buffers
+ * or staging slots could not be allocated), RNG_ECUDA.  A host-output call
+ * that fails part-way leaves the streams partly advanced: the generator
+ * then refuses further generation with RNG_ESTATE until rng_init. */
 int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev,
                  uint64_t *out_host, rng_err **err);
 
@@ -383,7 +386,7 @@ typedef struct rng_server_opts {
     uint32_t struct_size;
     uint32_t max_active;          /* requests admitted at once; default 1024 */
     uint64_t hbm_budget_bytes;    /* device arena for outputs and states; default 64 GiB */
-    uint64_t step_bytes;          /* output bytes one step aims to produce; default 512 MiB */
+    uint64_t step_bytes;          /* output bytes one step aims to produce; default 2 GiB */
     uint32_t max_steps_in_flight; /* launched, unfinished steps; default 2 */
     uint32_t values_per_thread;   /* 1..32 (power of two); 0 = 8 */
     uint32_t max_units_per_step;  /* work-table capacity per step; default 1<<20 */

@@ -315,7 +315,7 @@ void rng_server_opts_default(rng_server_opts *o) {
   o->struct_size = sizeof(rng_server_opts);
   o->max_active = 1024;
   o->hbm_budget_bytes = uint64_t(64) << 30;
-  o->step_bytes = uint64_t(512) << 20;
+  o->step_bytes = uint64_t(2) << 30;
   o->max_steps_in_flight = 2;
   o->values_per_thread = 8;
   o->max_units_per_step = 1u << 20;

@@ -288,6 +288,27 @@ def test_ring_output_holds_the_last_rows(n, T, R):
     assert np.array_equal(after, want[T:])
 
 
+def test_allocation_failure_is_reported_and_recoverable():
+    # A device buffer far larger than the GPU: cudaMalloc fails, the call
+    # returns RNG_ENOMEM, and the generator still works for device output
+    # after rng_init.
+    n = 1000
+    g = rng.Generator(n, 2, device_buffer_bytes=1 << 50, host_path=1)
+    with pytest.raises(rng.RngError) as e:
+        g.generate_to_host(3)
+    assert e.value.code == 2
+    g.init()
+    assert np.array_equal(g.generate(3).cpu().numpy(), oracle.generate(n, 2, 3))
+    g.close()
+
+
+def test_server_arena_allocation_failure():
+    from paper_1609_01257_gb300 import _capi as C
+    with pytest.raises(rng.RngError) as e:
+        rng.Server(hbm_budget_bytes=1 << 50)
+    assert e.value.code == C.RNG_ENOMEM
+
+
 def test_live_objects_balance():
     before = rng.live_objects()
     gs = [rng.Generator(100, k) for k in range(3)]
