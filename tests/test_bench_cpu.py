@@ -1,0 +1,34 @@
+"""Host-side pieces of bench.py: clock-sample parsing, the traffic lookup
+(reported only while the kernel sources match the capture), peaks."""
+import os
+
+import bench
+
+
+def test_parse_clock_samples():
+    text = """0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active
+0, 1980, 2070, 1100.0, 0x4, Not Active, Not Active, Not Active, Active
+0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active
+garbage line
+"""
+    c = bench.parse_clock_samples(text)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.parse_clock_samples("") is None
+
+
+def test_traffic_lookup_tracks_kernel_sources(tmp_path, monkeypatch):
+    f = tmp_path / "t.md"
+    f.write_text(f"kernel_source_sha256_16: {bench._kernel_source_hash()}\n"
+                 "traffic_bytes_per_launch[streaming]: 3.5e+10\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench._traffic_per_launch("streaming") == 3.5e10
+    assert bench._traffic_per_launch("plain") is None
+    f.write_text("kernel_source_sha256_16: 0000000000000000\ntraffic_bytes_per_launch[streaming]: 3.5e+10\n")
+    assert bench._traffic_per_launch("streaming") is None
+
+
+def test_peaks_file_is_read():
+    peaks, src = bench._peaks()
+    assert peaks["hbm_gbs"] > 0
+    if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
+        assert src == "measured"
