@@ -294,11 +294,15 @@ typedef struct rng_batch rng_batch;
 
 typedef struct rng_batch_opts {
     uint32_t struct_size;
-    uint32_t values_per_thread;  /* 0 = autotune over {1,2,4,8,16,32} */
+    uint32_t values_per_thread;  /* 1, 2, 4, 6, 8, 12, 16, 24 or 32; 0 = autotune */
     uint32_t block_threads;      /* 0 = 256 */
     uint32_t tune_reps;          /* timed replays per candidate (default 3) */
     void *stream;                /* cudaStream_t; NULL = own stream */
     int32_t device;              /* -1 = current */
+    uint32_t mode;               /* work distribution: 0 = autotune (both),
+                                    1 = one work unit per block (the hardware
+                                    hands units out in order), 2 = persistent
+                                    blocks taking units from a device counter */
 } rng_batch_opts;
 
 void rng_batch_opts_default(rng_batch_opts *opts);
@@ -317,10 +321,12 @@ int rng_batch_create(uint32_t count, const uint64_t *streams,
 /* Replays the captured graph on the batch's stream; asynchronous. */
 int rng_batch_run(rng_batch *b, rng_err **err);
 int rng_batch_sync(rng_batch *b, rng_err **err);
-/* Chosen shape and the tuned time of one replay (ms; 0 if not tuned). */
+/* Chosen shape -- values per thread, block size, grid, work units, work
+ * distribution (1 = one unit per block, 2 = persistent blocks with a
+ * counter) -- and the tuned time of one replay (ms; 0 if not tuned). */
 int rng_batch_config(const rng_batch *b, uint32_t *values_per_thread,
                      uint32_t *block_threads, uint32_t *grid_blocks,
-                     uint64_t *work_units, double *tuned_ms);
+                     uint64_t *work_units, uint32_t *mode, double *tuned_ms);
 void *rng_batch_stream(rng_batch *b);
 void rng_batch_destroy(rng_batch *b);
 

@@ -56,6 +56,7 @@ class RngBatchOpts(ctypes.Structure):
         ("tune_reps", c_u32),
         ("stream", c_vp),
         ("device", c_i32),
+        ("mode", c_u32),
     ]
 
 
@@ -132,7 +133,7 @@ SIGNATURES = {
     "rng_batch_run": ([c_vp, P_err], c_int),
     "rng_batch_sync": ([c_vp, P_err], c_int),
     "rng_batch_config": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32), ctypes.POINTER(c_u32),
-                          P_u64, ctypes.POINTER(c_dbl)], c_int),
+                          P_u64, ctypes.POINTER(c_u32), ctypes.POINTER(c_dbl)], c_int),
     "rng_batch_stream": ([c_vp], c_vp),
     "rng_batch_destroy": ([c_vp], None),
     "rng_batch_generate_noalloc": ([c_u32, P_u64, P_u64, P_u64, ctypes.POINTER(c_vp), c_vp, P_err], c_int),

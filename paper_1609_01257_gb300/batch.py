@@ -17,7 +17,7 @@ class Batch:
 
     def __init__(self, streams: Sequence[int], iterations: Sequence[int], seeds: Sequence[int], *,
                  outputs: Optional[List[torch.Tensor]] = None, values_per_thread: int = 0,
-                 tune_reps: int = 3, stream=None, device: Optional[int] = None):
+                 tune_reps: int = 3, mode: int = 0, stream=None, device: Optional[int] = None):
         lib = C.load()
         k = len(streams)
         assert len(iterations) == k and len(seeds) == k and k > 0
@@ -32,6 +32,7 @@ class Batch:
         lib.rng_batch_opts_default(ctypes.byref(o))
         o.values_per_thread = values_per_thread
         o.tune_reps = tune_reps
+        o.mode = mode
         if stream is None:
             stream = torch.cuda.Stream(device=self.device)  # pooled by torch, never destroyed
         self._torch_stream = stream
@@ -58,11 +59,11 @@ class Batch:
 
     def config(self):
         v, b, g = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-        u, ms = ctypes.c_uint64(), ctypes.c_double()
+        u, ms, m = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint32()
         self._lib.rng_batch_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(g), ctypes.byref(u),
-                                   ctypes.byref(ms))
+                                   ctypes.byref(m), ctypes.byref(ms))
         return {"values_per_thread": v.value, "block_threads": b.value, "grid_blocks": g.value,
-                "work_units": u.value, "tuned_ms": ms.value}
+                "work_units": u.value, "tuned_ms": ms.value, "one_unit_per_block": m.value == 1}
 
     def close(self):
         if self._h:

@@ -29,6 +29,7 @@ struct rng_batch {
   uint32_t *d_counter = nullptr;
   uint32_t n_units = 0;
   uint32_t vpt = 0, block = 256, grid = 0;
+  bool per_block = false;  // one unit per block (no counter) instead of a persistent grid
   double tuned_ms = 0.0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -46,7 +47,7 @@ void drop_graph(rng_batch *b) {
 }
 
 // Builds the unit table for `vpt`, uploads it and captures the graph.
-int prepare(rng_batch *b, uint32_t vpt, rng_err **err) {
+int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
   const uint64_t tile = uint64_t(kBlock) * vpt;
   std::vector<rngi::BatchUnit> units;
   for (uint32_t k = 0; k < b->inst.size(); ++k)
@@ -78,14 +79,16 @@ int prepare(rng_batch *b, uint32_t vpt, rng_err **err) {
   b->block = kBlock;
   const int per_sm = rngi::batch_blocks_per_sm(vpt, kBlock);
   const uint64_t resident = uint64_t(rngi::device_sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
-  b->grid = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(resident, b->n_units)));
+  b->per_block = per_block;
+  b->grid = per_block ? b->n_units
+                      : static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(resident, b->n_units)));
 
   drop_graph(b);
   cudaError_t st = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (st == cudaSuccess) {
-    cudaError_t s1 = cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), b->stream);
-    cudaError_t s2 = rngi::launch_batch(b->d_inst, b->d_units, b->n_units, b->d_counter, vpt, kBlock,
-                                        b->grid, b->stream);
+    cudaError_t s1 = per_block ? cudaSuccess : cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), b->stream);
+    cudaError_t s2 = rngi::launch_batch(b->d_inst, b->d_units, b->n_units, per_block ? nullptr : b->d_counter,
+                                        vpt, kBlock, b->grid, b->stream);
     st = cudaStreamEndCapture(b->stream, &b->graph);
     if (st == cudaSuccess) st = s1 != cudaSuccess ? s1 : s2;
   }
@@ -112,6 +115,7 @@ void rng_batch_opts_default(rng_batch_opts *o) {
   o->tune_reps = 3;
   o->stream = nullptr;
   o->device = -1;
+  o->mode = 0;
 }
 
 int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *iterations,
@@ -132,6 +136,7 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
   if (v && !rngi::batch_vpt_supported(v))
     return rngi::fail(err, RNG_EINVAL,
                       "rng_batch_create: values_per_thread must be 0 or one of 1, 2, 4, 6, 8, 12, 16, 24, 32");
+  if (o.mode > 2) return rngi::fail(err, RNG_EINVAL, "rng_batch_create: mode must be 0, 1 or 2");
   if (o.block_threads && o.block_threads != kBlock)
     return rngi::fail(err, RNG_EINVAL, "rng_batch_create: block_threads must be 0 or 256");
   for (uint32_t k = 0; k < count; ++k) {
@@ -176,7 +181,7 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     rc = rngi::cuda_fail(err, cudaMemcpyAsync(b->d_inst, b->inst.data(), count * sizeof(rngi::BatchInstance),
                                               cudaMemcpyHostToDevice, b->stream),
                          "cudaMemcpy(batch)");
-  if (!rc && v) rc = prepare(b, v, err);
+  if (!rc && v) rc = prepare(b, v, o.mode == 1, err);
   if (!rc && !v) {
     // Autotune: time each candidate's graph and keep the fastest.
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -184,10 +189,15 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     if (!rc) rc = rngi::cuda_fail(err, cudaEventCreate(&e1), "cudaEventCreate");
     const uint32_t reps = o.tune_reps ? o.tune_reps : 3;
     uint32_t best_v = 0;
+    bool best_pb = false;
     double best_ms = 0.0;
-    for (uint32_t cand : {1u, 2u, 4u, 6u, 8u, 12u, 16u, 24u, 32u}) {
-      if (rc) break;
-      rc = prepare(b, cand, err);
+    for (int k = 0; k < 18 && !rc; ++k) {
+      static const uint32_t cands[] = {1u, 2u, 4u, 6u, 8u, 12u, 16u, 24u, 32u};
+      const uint32_t cand = cands[k % 9];
+      const bool pb = k >= 9;
+      if (o.mode == 1 && !pb) continue;
+      if (o.mode == 2 && pb) continue;
+      rc = prepare(b, cand, pb, err);
       if (!rc) rc = replay(b, err);  // warm-up
       if (!rc) rc = rngi::cuda_fail(err, cudaEventRecord(e0, b->stream), "cudaEventRecord");
       for (uint32_t r = 0; r < reps && !rc; ++r) rc = replay(b, err);
@@ -197,12 +207,13 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
       if (!rc) rc = rngi::cuda_fail(err, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
       if (!rc && (best_v == 0 || ms / reps < best_ms)) {
         best_v = cand;
+        best_pb = pb;
         best_ms = ms / reps;
       }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (!rc) rc = prepare(b, best_v, err);
+    if (!rc) rc = prepare(b, best_v, best_pb, err);
     if (!rc) b->tuned_ms = best_ms;
   }
   if (rc) {
@@ -225,8 +236,9 @@ int rng_batch_sync(rng_batch *b, rng_err **err) {
 }
 
 int rng_batch_config(const rng_batch *b, uint32_t *vpt, uint32_t *block, uint32_t *grid, uint64_t *units,
-                     double *tuned_ms) {
+                     uint32_t *mode, double *tuned_ms) {
   if (!b) return RNG_EINVAL;
+  if (mode) *mode = b->per_block ? 1u : 2u;
   if (vpt) *vpt = b->vpt;
   if (block) *block = b->block;
   if (grid) *grid = b->grid;

@@ -14,6 +14,7 @@
 #include <string.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -58,6 +59,10 @@ struct rng_gen {
   rngi::LaunchShape chunk_shape{};  // shape of the last streamed chunk width
   uint64_t chunk_span = 0;
   uint64_t *d_state = nullptr;
+  uint64_t *d_state2 = nullptr;      // second state array for banded launches
+  uint64_t *d_jump = nullptr;        // GF(2) jump matrices for banded launches
+  uint64_t jump_rows = 0;            // band_rows the table on the device is for
+  uint32_t jump_count = 0;           // matrices in that table
   cudaStream_t compute = nullptr, copy = nullptr;
   bool own_compute = false;
   uint64_t *d_buf[2] = {nullptr, nullptr};
@@ -118,6 +123,58 @@ int profile_restart(rng_gen *g, rng_err **err) {
     if (rc) return rc;
   }
   return rngi::cuda_fail(err, cudaEventRecord(g->origin, g->compute), "cudaEventRecord");
+}
+
+constexpr uint32_t kMaxJumpMatrices = 64;
+
+// Launches the row kernel for `a`.  When the launch covers every stream but
+// has too few tiles to fill the GPU, its rows are split into bands run by
+// separate blocks: each band's blocks jump their states ahead over GF(2),
+// and the final states are written to the second state array, which then
+// becomes the current one.
+int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh, rng_err **err) {
+  a.band_rows = 0;
+  a.jump = nullptr;
+  a.state_out = a.state;
+  bool swap = false;
+  if (!a.ring_rows && a.out && a.s_begin == 0 && a.s_end == g->n) {
+    const uint64_t br = rngi::choose_band_rows(g->n, a.rows, sh, g->device);
+    if (br) {
+      const uint64_t bands = (a.rows + br - 1) / br;
+      uint32_t count = 0;
+      while ((uint64_t(1) << count) < bands) ++count;  // bits of band indices 0 .. bands-1
+      if (count == 0) count = 1;
+      int rc = RNG_OK;
+      if (!g->d_state2)
+        rc = rngi::cuda_fail(err, cudaMalloc(&g->d_state2, g->n * 8), "cudaMalloc(second state array)");
+      if (!rc && !g->d_jump)
+        rc = rngi::cuda_fail(err, cudaMalloc(&g->d_jump, kMaxJumpMatrices * 64 * 8), "cudaMalloc(jump table)");
+      if (rc) return rc;
+      if (g->jump_rows != br || g->jump_count < count) {
+        std::vector<uint64_t> cols(size_t(count) * 64);
+        rngi::jump_table(br, count, cols.data());
+        // Pageable source: the call returns once the source has been read.
+        rc = rngi::cuda_fail(err, cudaMemcpyAsync(g->d_jump, cols.data(), cols.size() * 8, cudaMemcpyHostToDevice,
+                                                  g->compute),
+                             "jump table upload");
+        if (rc) return rc;
+        g->jump_rows = br;
+        g->jump_count = count;
+      }
+      a.band_rows = br;
+      a.jump = g->d_jump;
+      if (a.write_state) {
+        a.state_out = g->d_state2;
+        swap = true;
+      }
+    }
+  }
+  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
+  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute);
+  op_end(g, op, g->compute);
+  int rc = rngi::cuda_fail(err, st, "rows kernel launch");
+  if (!rc && swap) std::swap(g->d_state, g->d_state2);
+  return rc;
 }
 
 int ensure_buffers(rng_gen *g, bool staged, rng_err **err) {
@@ -191,10 +248,7 @@ int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_
     g->chunk_span = c.span;
   }
   const rngi::LaunchShape sh = g->chunk_shape;
-  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute);
-  op_end(g, op, g->compute);
-  return rngi::cuda_fail(err, st, "rows kernel launch");
+  return gen_launch_rows(g, a, sh, err);
 }
 
 // Host consumer thread for staged output (pageable destination or sink).
@@ -402,10 +456,7 @@ int direct_host(rng_gen *g, uint64_t T, uint64_t *dst, rng_err **err) {
   a.key = g->key;
   a.from_hash = !g->materialized;
   a.write_state = 1;
-  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
-  op_end(g, op, g->compute);
-  int rc = rngi::cuda_fail(err, st, "rows kernel launch (direct to host)");
+  int rc = gen_launch_rows(g, a, g->shape, err);
   if (rc) return rc;
   g->materialized = true;
   g->pos += T;
@@ -523,6 +574,8 @@ void rng_destroy(rng_gen *g) {
   if (g->compute) cudaStreamSynchronize(g->compute);
   if (g->copy) cudaStreamSynchronize(g->copy);
   cudaFree(g->d_state);
+  cudaFree(g->d_state2);
+  cudaFree(g->d_jump);
   for (int b = 0; b < 2; ++b) {
     cudaFree(g->d_buf[b]);
     if (g->produced[b]) cudaEventDestroy(g->produced[b]);
@@ -586,10 +639,7 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   a.key = g->key;
   a.from_hash = !g->materialized;
   a.write_state = 1;
-  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
-  op_end(g, op, g->compute);
-  rc = rngi::cuda_fail(err, st, "rows kernel launch");
+  rc = gen_launch_rows(g, a, g->shape, err);
   if (rc) return rc;
   g->materialized = true;
   g->pos += iterations;
@@ -618,10 +668,7 @@ int rng_generate_ring(rng_gen *g, uint64_t iterations, uint64_t *ring_dev, uint6
   a.from_hash = !g->materialized;
   a.write_state = 1;
   a.ring_rows = ring_rows;
-  long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, g->shape, static_cast<int>(g->opts.store_policy), g->compute);
-  op_end(g, op, g->compute);
-  rc = rngi::cuda_fail(err, st, "rows kernel launch (ring)");
+  rc = gen_launch_rows(g, a, g->shape, err);
   if (rc) return rc;
   g->materialized = true;
   g->pos += iterations;

@@ -15,7 +15,9 @@ constexpr int kStoreDefault = 0;     // st.global
 constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
 
 // Kernel entry points (kernels.cu); nullptr for shapes that are not compiled.
-const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block);
+// banded: the variant that splits rows into bands (few values per thread
+// only; store policy is always streaming there).
+const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded = false);
 const void *checksum_kernel_fn(uint32_t vpt);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *init_kernel_fn();
@@ -45,6 +47,9 @@ struct RowsLaunch {
   int from_hash;        // initial state from the hash instead of `state`
   int write_state;      // store the advanced states back
   uint64_t ring_rows;   // 0, or rows wrap around a ring of this many rows
+  uint64_t band_rows;   // 0, or rows are split into bands of this many rows
+  const uint64_t *jump; // bands: matrices M^(band_rows * 2^b), 64 columns each
+  uint64_t *state_out;  // where final states go (== state unless banded)
 };
 
 struct LaunchShape {
@@ -102,6 +107,12 @@ cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint
                          uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
                          cudaStream_t st);
 int batch_blocks_per_sm(uint32_t vpt, uint32_t block);
+// Rows per band when a launch should split its rows across blocks (few
+// streams, many rows: too few tiles to fill the GPU); 0 for no split.
+uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device);
+// Host-side GF(2) tables for banded launches: writes `count` matrices
+// M^(band_rows * 2^b), b = 0 .. count-1, as 64 column words each.
+void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols);
 // Values per thread the work-list kernel is compiled for.
 bool batch_vpt_supported(uint32_t vpt);
 

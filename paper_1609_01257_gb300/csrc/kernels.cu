@@ -117,39 +117,86 @@ __device__ __forceinline__ void load_tile(uint64_t (&st)[VPT], const RowsLaunch 
 }
 
 template <int VPT, int P, int BLOCK = kBlock>
-__device__ __forceinline__ void store_tile_state(const uint64_t (&st)[VPT], const RowsLaunch &a,
+__device__ __forceinline__ void store_tile_state(const uint64_t (&st)[VPT], uint64_t *dst, const RowsLaunch &a,
                                                  uint64_t rel0, uint64_t span) {
 #pragma unroll
   for (int j = 0; j < VPT / P; ++j)
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const uint64_t rel = rel0 + slot_offset<P, BLOCK>(j, q);
-      if (rel < span) a.state[a.s_begin + rel] = st[j * P + q];
+      if (rel < span) dst[a.s_begin + rel] = st[j * P + q];
     }
 }
 
-// Persistent row kernel: blocks walk the tiles of blockDim * VPT streams;
-// each thread holds VPT states in registers across all rows of its tile.
-template <int VPT, int W, int POLICY, int BLOCK>
+// Advances the states by band * band_rows iterations: for each set bit b of
+// `band`, one multiplication over GF(2) by M^(band_rows * 2^b), whose 64
+// columns are jump[64 b .. 64 b + 63] (the same for every thread: broadcast
+// loads).  One state at a time, so the extra registers do not scale with VPT.
+template <int VPT>
+__device__ __forceinline__ void jump_states(uint64_t (&st)[VPT], const uint64_t *__restrict__ jump,
+                                            uint64_t band) {
+  for (int b = 0; band; ++b, band >>= 1) {
+    if (!(band & 1)) continue;
+    const uint64_t *col = jump + 64 * b;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const uint64_t x = st[v];
+      uint64_t acc = 0;
+#pragma unroll 8
+      for (int j = 0; j < 64; ++j) acc ^= __ldg(col + j) & (0ull - ((x >> j) & 1ull));
+      st[v] = acc;
+    }
+  }
+}
+
+// Row kernel.  Unbanded (BANDED = false): a work unit is a tile of BLOCK *
+// VPT streams with all rows; each thread holds VPT states in registers
+// across all rows.  Banded: a unit is (tile, band of band_rows rows); the
+// unit jumps its states ahead to the band's first row, and the final states
+// (from the last band) go to state_out, which must not alias `state` (other
+// bands still read the starting states).  Blocks stride over units when the
+// grid is smaller than the unit count.
+template <int VPT, int W, int POLICY, int BLOCK, bool BANDED>
 __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
   const uint64_t span = a.s_end - a.s_begin;
   const uint64_t tile_vals = static_cast<uint64_t>(BLOCK) * VPT;
   const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const uint64_t rel0 = tile * tile_vals;
-    uint64_t st[VPT];
-    load_tile<VPT, W, BLOCK>(st, a, rel0, span);
-    if (a.out) {
-      if (rel0 + tile_vals <= span)
-        emit_rows<VPT, W, POLICY, false, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
-      else
-        emit_rows<VPT, W, POLICY, true, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
-    } else {
-      for (uint64_t r = 0; r < a.rows; ++r)
+  if constexpr (!BANDED) {
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const uint64_t rel0 = tile * tile_vals;
+      uint64_t st[VPT];
+      load_tile<VPT, W, BLOCK>(st, a, rel0, span);
+      if (a.out) {
+        if (rel0 + tile_vals <= span)
+          emit_rows<VPT, W, POLICY, false, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
+        else
+          emit_rows<VPT, W, POLICY, true, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
+      } else {
+        for (uint64_t r = 0; r < a.rows; ++r)
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+          for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+      }
+      if (a.write_state) store_tile_state<VPT, W, BLOCK>(st, a.state, a, rel0, span);
     }
-    if (a.write_state) store_tile_state<VPT, W, BLOCK>(st, a, rel0, span);
+  } else {
+    const uint64_t band_rows = a.band_rows;
+    const uint64_t n_bands = (a.rows + band_rows - 1) / band_rows;
+    for (uint64_t w = blockIdx.x; w < n_tiles * n_bands; w += gridDim.x) {
+      const uint64_t tile = w % n_tiles;
+      const uint64_t band = w / n_tiles;
+      const uint64_t rel0 = tile * tile_vals;
+      uint64_t st[VPT];
+      load_tile<VPT, W, BLOCK>(st, a, rel0, span);
+      if (band) jump_states<VPT>(st, a.jump, band);
+      const uint64_t r0 = band * band_rows;
+      const uint64_t rows = a.rows - r0 < band_rows ? a.rows - r0 : band_rows;
+      uint64_t *out = a.out + r0 * a.pitch;
+      if (rel0 + tile_vals <= span)
+        emit_rows<VPT, W, POLICY, false, BLOCK>(st, out, a.pitch, rows, rel0, span);
+      else
+        emit_rows<VPT, W, POLICY, true, BLOCK>(st, out, a.pitch, rows, rel0, span);
+      if (a.write_state && band == n_bands - 1) store_tile_state<VPT, W, BLOCK>(st, a.state_out, a, rel0, span);
+    }
   }
 }
 
@@ -240,18 +287,69 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
     }
     // Values past the end of the range were loaded as 0 and advance to 0,
     // so they add nothing; the states of real streams are written back.
-    if (a.write_state) store_tile_state<VPT, 1>(st, a, rel0, span);
+    if (a.write_state) store_tile_state<VPT, 1>(st, a.state, a, rel0, span);
     __syncthreads();
   }
 }
 
-// Work-list persistent kernel (batched and served forms): blocks take work
-// units (one tile of streams of one chunk) from a shared counter -- the
-// table lists the largest units first -- and emit all rows of the unit.
+// One work unit of the work-list kernel: one tile of streams of one chunk,
+// all rows of the chunk.
+template <int VPT>
+__device__ __forceinline__ void process_unit(const BatchInstance *__restrict__ inst,
+                                             const BatchUnit *__restrict__ units, uint32_t u) {
+  const BatchUnit wu = units[u];
+  const BatchInstance in = inst[wu.inst];
+  RowsLaunch a;
+  a.state = in.state;
+  a.out = in.out;
+  a.pitch = in.streams;
+  a.s_begin = wu.s_begin;
+  a.s_end = wu.s_begin + wu.count;
+  a.id_base = 0;
+  a.rows = in.rows;
+  a.key = in.key;
+  a.from_hash = in.from_hash;
+  a.write_state = in.write_state;
+  a.ring_rows = 0;
+  const uint64_t span = wu.count;
+  const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  uint64_t *row = in.out + wu.s_begin;
+  // 16-byte stores for few values per thread on aligned rows; one streaming
+  // 8-byte store per value otherwise (the faster form once a thread holds six
+  // or more streams).
+  if (VPT % 2 == 0 && VPT < 6 && in.vec) {
+    constexpr int V2 = VPT >= 2 ? VPT : 2;
+    uint64_t st[V2];
+    load_tile<V2, 2>(st, a, 0, span);
+    if (span == tile_vals)
+      emit_rows<V2, 2, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
+    else
+      emit_rows<V2, 2, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
+    if (a.write_state) store_tile_state<V2, 2>(st, a.state, a, 0, span);
+  } else {
+    uint64_t st[VPT];
+    load_tile<VPT, 1>(st, a, 0, span);
+    if (span == tile_vals)
+      emit_rows<VPT, 1, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
+    else
+      emit_rows<VPT, 1, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
+    if (a.write_state) store_tile_state<VPT, 1>(st, a.state, a, 0, span);
+  }
+}
+
+// Work-list kernel (batched, served and allocation-free forms).  With a
+// counter, a persistent grid of blocks takes units from it; without one
+// (counter == nullptr), block b runs unit b and the hardware hands units out
+// in table order as blocks finish.  Either way the table lists the largest
+// units first.
 template <int VPT>
 __global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *__restrict__ inst,
                                                           const BatchUnit *__restrict__ units,
                                                           uint32_t n_units, uint32_t *counter) {
+  if (counter == nullptr) {
+    if (blockIdx.x < n_units) process_unit<VPT>(inst, units, blockIdx.x);
+    return;
+  }
   __shared__ uint32_t s_unit;
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
@@ -259,51 +357,15 @@ __global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *_
     const uint32_t u = s_unit;
     __syncthreads();
     if (u >= n_units) return;
-    const BatchUnit wu = units[u];
-    const BatchInstance in = inst[wu.inst];
-    RowsLaunch a;
-    a.state = in.state;
-    a.out = in.out;
-    a.pitch = in.streams;
-    a.s_begin = wu.s_begin;
-    a.s_end = wu.s_begin + wu.count;
-    a.id_base = 0;
-    a.rows = in.rows;
-    a.key = in.key;
-    a.from_hash = in.from_hash;
-    a.write_state = in.write_state;
-    const uint64_t span = wu.count;
-    const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
-    uint64_t *row = in.out + wu.s_begin;
-    // 16-byte stores for few values per thread on aligned rows; one
-    // streaming 8-byte store per value otherwise (the faster form once a
-    // thread holds six or more streams).
-    if (VPT % 2 == 0 && VPT < 6 && in.vec) {
-      constexpr int V2 = VPT >= 2 ? VPT : 2;
-      uint64_t st[V2];
-      load_tile<V2, 2>(st, a, 0, span);
-      if (span == tile_vals)
-        emit_rows<V2, 2, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
-      else
-        emit_rows<V2, 2, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
-      if (a.write_state) store_tile_state<V2, 2>(st, a, 0, span);
-    } else {
-      uint64_t st[VPT];
-      load_tile<VPT, 1>(st, a, 0, span);
-      if (span == tile_vals)
-        emit_rows<VPT, 1, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
-      else
-        emit_rows<VPT, 1, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
-      if (a.write_state) store_tile_state<VPT, 1>(st, a, 0, span);
-    }
+    process_unit<VPT>(inst, units, u);
   }
 }
 
 template <int VPT, int W>
 const void *rows_fn_policy(int policy) {
   return policy == kPolicyStreaming
-             ? reinterpret_cast<const void *>(&rows_kernel<VPT, W, kPolicyStreaming, kBlock>)
-             : reinterpret_cast<const void *>(&rows_kernel<VPT, W, kPolicyDefault, kBlock>);
+             ? reinterpret_cast<const void *>(&rows_kernel<VPT, W, kPolicyStreaming, kBlock, false>)
+             : reinterpret_cast<const void *>(&rows_kernel<VPT, W, kPolicyDefault, kBlock, false>);
 }
 
 // Larger blocks (one store per value, streaming policy): wider contiguous
@@ -311,13 +373,13 @@ const void *rows_fn_policy(int policy) {
 template <int BLOCK>
 const void *rows_fn_wide(uint32_t vpt) {
   switch (vpt) {
-    case 2: return reinterpret_cast<const void *>(&rows_kernel<2, 1, kPolicyStreaming, BLOCK>);
-    case 4: return reinterpret_cast<const void *>(&rows_kernel<4, 1, kPolicyStreaming, BLOCK>);
-    case 6: return reinterpret_cast<const void *>(&rows_kernel<6, 1, kPolicyStreaming, BLOCK>);
-    case 8: return reinterpret_cast<const void *>(&rows_kernel<8, 1, kPolicyStreaming, BLOCK>);
-    case 12: return reinterpret_cast<const void *>(&rows_kernel<12, 1, kPolicyStreaming, BLOCK>);
-    case 16: return reinterpret_cast<const void *>(&rows_kernel<16, 1, kPolicyStreaming, BLOCK>);
-    case 24: return reinterpret_cast<const void *>(&rows_kernel<24, 1, kPolicyStreaming, BLOCK>);
+    case 2: return reinterpret_cast<const void *>(&rows_kernel<2, 1, kPolicyStreaming, BLOCK, false>);
+    case 4: return reinterpret_cast<const void *>(&rows_kernel<4, 1, kPolicyStreaming, BLOCK, false>);
+    case 6: return reinterpret_cast<const void *>(&rows_kernel<6, 1, kPolicyStreaming, BLOCK, false>);
+    case 8: return reinterpret_cast<const void *>(&rows_kernel<8, 1, kPolicyStreaming, BLOCK, false>);
+    case 12: return reinterpret_cast<const void *>(&rows_kernel<12, 1, kPolicyStreaming, BLOCK, false>);
+    case 16: return reinterpret_cast<const void *>(&rows_kernel<16, 1, kPolicyStreaming, BLOCK, false>);
+    case 24: return reinterpret_cast<const void *>(&rows_kernel<24, 1, kPolicyStreaming, BLOCK, false>);
     default: return nullptr;
   }
 }
@@ -337,6 +399,24 @@ const void *rows_fn_dispatch(int width, int policy) {
 #define RNG_FOR_EACH_VPT(X) \
   X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) \
   X(32) X(36) X(40) X(48) X(64)
+
+// Banded variants (few streams, many rows): 256-thread blocks, streaming
+// stores, the widest store width for the values per thread.
+const void *select_rows_banded(uint32_t vpt, int width) {
+  switch (vpt) {
+    case 1: return reinterpret_cast<const void *>(&rows_kernel<1, 1, kPolicyStreaming, kBlock, true>);
+    case 2:
+      return width >= 2 ? reinterpret_cast<const void *>(&rows_kernel<2, 2, kPolicyStreaming, kBlock, true>)
+                        : reinterpret_cast<const void *>(&rows_kernel<2, 1, kPolicyStreaming, kBlock, true>);
+    case 4:
+      return width >= 4   ? reinterpret_cast<const void *>(&rows_kernel<4, 4, kPolicyStreaming, kBlock, true>)
+             : width >= 2 ? reinterpret_cast<const void *>(&rows_kernel<4, 2, kPolicyStreaming, kBlock, true>)
+                          : reinterpret_cast<const void *>(&rows_kernel<4, 1, kPolicyStreaming, kBlock, true>);
+    case 8: return reinterpret_cast<const void *>(&rows_kernel<8, 1, kPolicyStreaming, kBlock, true>);
+    case 16: return reinterpret_cast<const void *>(&rows_kernel<16, 1, kPolicyStreaming, kBlock, true>);
+    default: return nullptr;
+  }
+}
 
 const void *select_rows(uint32_t vpt, int width, int policy, uint32_t block = kBlock) {
   if (block == 512) return rows_fn_wide<512>(vpt);
@@ -386,7 +466,8 @@ const void *select_batch(uint32_t vpt) {
 
 // Kernel entry points for the host-side launch code (launch.cpp); nullptr
 // when a shape is not compiled.
-const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block) {
+const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded) {
+  if (banded) return block == kBlock ? select_rows_banded(vpt, width) : nullptr;
   return select_rows(vpt, width, policy, block);
 }
 const void *checksum_kernel_fn(uint32_t vpt) { return select_checksum(vpt); }

@@ -80,6 +80,8 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
 }
 
 cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st) {
+  if (a.band_rows && (a.ring_rows || !a.jump || (a.write_state && a.state_out == a.state)))
+    return cudaErrorInvalidValue;
   // Widest store the output's alignment allows: every row must start on an
   // 8*W-byte boundary (pitch a multiple of W, base aligned to 8*W bytes).
   int width = 1;
@@ -90,11 +92,19 @@ cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_po
       break;
     }
   if (width > static_cast<int>(sh.width)) width = static_cast<int>(sh.width);
-  const void *fn = rows_kernel_fn(sh.vpt, width, store_policy, sh.block);
+  const void *fn = rows_kernel_fn(sh.vpt, width, store_policy, sh.block, a.band_rows != 0);
   if (!fn) return cudaErrorInvalidValue;
   RowsLaunch args = a;
   void *params[] = {&args};
-  cudaError_t e = cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), params, 0, st);
+  uint64_t grid = sh.grid;
+  if (a.band_rows) {
+    // One block per (tile, band) unit, unless the shape asked for fewer.
+    const uint64_t span = a.s_end - a.s_begin;
+    const uint64_t tiles = (span + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
+    const uint64_t units = tiles * ((a.rows + a.band_rows - 1) / a.band_rows);
+    if (grid >= tiles) grid = units < 0x7fffffffull ? units : 0x7fffffffull;
+  }
+  cudaError_t e = cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(sh.block), params, 0, st);
   if (e == cudaSuccess) count_launch();
   return e;
 }
@@ -149,6 +159,27 @@ Gf2 update_power(uint64_t k) {
 }
 
 }  // namespace
+
+void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols) {
+  Gf2 m = update_power(band_rows);
+  for (uint32_t b = 0; b < count; ++b) {
+    for (int j = 0; j < 64; ++j) cols[64 * b + j] = m.col[j];
+    m = gf2_mul(m, m);
+  }
+}
+
+uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device) {
+  const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
+  const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
+  const uint64_t target = 2 * sms;            // blocks wanted in flight
+  const uint64_t min_band = 128;              // rows per band: amortises the jump
+  if (tiles * 2 >= target || rows < 2 * min_band) return 0;
+  if (!rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true)) return 0;  // no banded variant
+  uint64_t bands = (target + tiles - 1) / tiles;
+  if (bands > rows / min_band) bands = rows / min_band;
+  if (bands < 2) return 0;
+  return (rows + bands - 1) / bands;
+}
 
 cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key, int from_hash,
                         uint64_t k, cudaStream_t st) {

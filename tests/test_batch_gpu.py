@@ -14,14 +14,17 @@ def test_small_batch_fixed_vpt_all_values():
     streams = [1, 2, 3, 255, 256, 257, 1000, 4099, 70_000]
     iters = [1, 5, 2, 7, 3, 1, 9, 4, 2]
     seeds = [0, 1, 2, 3, 4, 5, 6, 7, 2**64 - 1]
-    for vpt in (1, 2, 4, 6, 8, 12, 16, 24, 32):
-        b = rng.Batch(streams, iters, seeds, values_per_thread=vpt)
-        b.run()
-        b.sync()
-        for k in range(len(streams)):
-            got = b.outputs[k].cpu().numpy()
-            assert np.array_equal(got, oracle.generate(streams[k], seeds[k], iters[k])), (vpt, k)
-        b.close()
+    want = [oracle.generate(streams[k], seeds[k], iters[k]) for k in range(len(streams))]
+    for mode in (1, 2):          # one unit per block / persistent blocks with a counter
+        for vpt in (1, 2, 4, 6, 8, 12, 16, 24, 32):
+            b = rng.Batch(streams, iters, seeds, values_per_thread=vpt, mode=mode)
+            b.run()
+            b.sync()
+            assert b.config()["one_unit_per_block"] == (mode == 1)
+            for k in range(len(streams)):
+                got = b.outputs[k].cpu().numpy()
+                assert np.array_equal(got, want[k]), (mode, vpt, k)
+            b.close()
 
 
 def test_replay_is_identical_and_autotuned():

@@ -288,6 +288,31 @@ def test_ring_output_holds_the_last_rows(n, T, R):
     assert np.array_equal(after, want[T:])
 
 
+@pytest.mark.parametrize("n,T", [(1, 5000), (5, 3000), (300, 2049), (4096, 1000), (10_000, 700), (70_001, 300)])
+def test_few_streams_many_rows_split_into_bands(n, T):
+    # Too few tiles to fill the GPU: rows are split into bands whose blocks
+    # jump ahead over GF(2); values and the final states must not change.
+    g = rng.Generator(n, 17)
+    a = g.generate(T).cpu().numpy()
+    b = g.generate(3).cpu().numpy()           # continues from the banded launch's states
+    g.close()
+    want = oracle.generate(n, 17, T + 3)
+    assert np.array_equal(a, want[:T])
+    assert np.array_equal(b, want[T:])
+
+
+@pytest.mark.parametrize("host_path", [1, 2])
+def test_few_streams_many_rows_to_host(host_path):
+    n, T = 1000, 3000
+    g = rng.Generator(n, 23, host_path=host_path)
+    host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
+    g.generate_to_host(T, host)
+    nxt = g.generate(2).cpu().numpy()
+    g.close()
+    want = oracle.generate(n, 23, T + 2)
+    assert np.array_equal(host.numpy(), want[:T]) and np.array_equal(nxt, want[T:])
+
+
 def test_allocation_failure_is_reported_and_recoverable():
     # A device buffer far larger than the GPU: cudaMalloc fails, the call
     # returns RNG_ENOMEM, and the generator still works for device output
