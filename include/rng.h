@@ -127,9 +127,12 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts,
                rng_gen **out, rng_err **err);
 
 /* Section 5, init kernel (Listing S4): state of stream g := hash of
- * (g0 + g) and the seed; position := 0.  Ordered on the compute stream;
- * returns before the device work completes.  Calling it again restarts
- * the streams. */
+ * (g0 + g) and the seed; position := 0.  With fuse_init (the default) no
+ * kernel runs here: the next generation launch hashes the ids in registers
+ * (the init values are iteration 0, so nothing is stored twice).  Otherwise
+ * the separate init kernel runs, ordered on the compute stream; the call
+ * returns before the device work completes.  Calling it again restarts the
+ * streams. */
 int rng_init(rng_gen *g, rng_err **err);
 
 /* Section 5, rng kernel (Listing S5) plus the device-side double buffer:
@@ -137,7 +140,8 @@ int rng_init(rng_gen *g, rng_err **err);
  * being the init value) and then advances p by `iterations`.
  * Exactly one of the two outputs is non-NULL:
  *  - out_dev: caller-owned device memory of at least 8*streams*iterations
- *    bytes, 8-byte aligned (16-byte alignment enables vector stores);
+ *    bytes, 8-byte aligned (shapes with few values per thread use 16- or
+ *    32-byte stores when rows are aligned to them);
  *    value (it - p) * streams + g.  Ordered on the compute stream; returns
  *    before the kernel completes.
  *  - out_host: caller-owned host memory of 8*streams*iterations bytes in
