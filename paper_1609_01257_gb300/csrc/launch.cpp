@@ -168,15 +168,16 @@ void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols) {
   }
 }
 
-// Bands only when the tiles cannot cover half the SMs; then about one
-// (tile, band) unit per SM, the shape that measured fastest for long runs
-// (128 tiles of 2^16 streams unbanded: 7.36 TB/s; three bands of them: 6.25).
+// Bands only when the tiles cannot cover half the SMs (128 unbanded tiles of
+// 2^16 streams ran at 7.37 TB/s, three bands of them at 6.25); then about
+// two (tile, band) units per SM (16 tiles of 4096 streams: 19 bands 6.6 TB/s,
+// 10 bands 4.7 TB/s).
 uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device) {
   const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
   const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
-  const uint64_t target = sms;                // units wanted in flight
+  const uint64_t target = 2 * sms;            // units wanted in flight
   const uint64_t min_band = 128;              // rows per band: amortises the jump
-  if (tiles * 2 >= target || rows < 2 * min_band) return 0;
+  if (tiles * 2 >= sms || rows < 2 * min_band) return 0;
   if (!rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true)) return 0;  // no banded variant
   uint64_t bands = (target + tiles - 1) / tiles;
   if (bands > rows / min_band) bands = rows / min_band;
