@@ -66,6 +66,25 @@ def test_unaligned_instance_outputs():
     b.close()
 
 
+def _row_checksums(block):
+    return np.bitwise_xor.reduce(block, axis=1), block.sum(axis=1, dtype=np.uint64)
+
+
+def test_paper_shaped_batch_every_row_checksummed():
+    # 512 instances, 8 GiB: every row of every instance reduced to its XOR and
+    # wrapping sum on the host and compared with the oracle's.
+    inst = workloads.batched_instances()
+    b = rng.Batch([i.streams for i in inst], [i.iterations for i in inst], [i.seed for i in inst])
+    b.run()
+    b.sync()
+    for k, ins in enumerate(inst):
+        out = b.outputs[k].cpu().numpy()
+        x, s = _row_checksums(out)
+        wx, ws, _ = oracle.row_checksums(ins.streams, ins.seed, ins.iterations)
+        assert np.array_equal(x, wx) and np.array_equal(s, ws), k
+    b.close()
+
+
 def test_paper_shaped_batch_sampled():
     # 512 instances, log-uniform sizes, 8 GiB total: every instance checked on
     # its first row and sampled values, small instances in full.

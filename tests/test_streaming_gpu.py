@@ -63,6 +63,25 @@ def test_direct_to_host_full_size_checksums():
         assert np.array_equal(x, wx[i0:i0 + 64]) and np.array_equal(s, ws[i0:i0 + 64]), i0
 
 
+def test_checksum_mode_largest_sweep_point():
+    # The sweep's largest point: 2^28 streams x 8 iterations in
+    # generate-and-checksum mode, in the launch shape the sweep times.  XOR
+    # against its closed form (the update is linear: XOR of row i is M^i
+    # applied to the XOR of the initial states), sum against the oracle.
+    from oracle import gf2
+    n, T, seed = 1 << 28, 8, 1
+    g = rng.Generator(n, seed)
+    rx, rs = g.generate_checksum(T)
+    g.sync()
+    rx, rs = rx.cpu().numpy(), rs.cpu().numpy()
+    g.close()
+    wx, ws, _ = oracle.row_checksums(n, seed, T)
+    assert np.array_equal(rx, wx) and np.array_equal(rs, ws)
+    m = gf2.xorshift_matrix()
+    for i in range(T):
+        assert int(rx[i]) == gf2.apply(gf2.power(m, i), int(wx[0]))
+
+
 def test_device_resident_full_size_sampled():
     # Same workload kept on the device (the benchmark's device leg): sampled
     # values one by one, plus the XOR checksum closed form on every row.
