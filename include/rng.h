@@ -365,7 +365,9 @@ void rng_batch_destroy(rng_batch *b);
  *
  * The first call on a device, with that device current, looks up the
  * scratch array's device address (cudaGetSymbolAddress) and caches it; make
- * that first call before any stream capture begins.  All calls share the one
+ * that first call before any stream capture begins.  A cudaDeviceReset
+ * destroys the array with the context, so do not call this entry point again
+ * on a device after resetting it in the same process.  All calls share the one
  * array and each call overwrites it, so calls whose work overlaps on the GPU
  * (launched on different streams without ordering between them) race and
  * produce wrong output; calls on one stream are ordered and safe.  The host

@@ -334,6 +334,19 @@ def test_server_arena_allocation_failure():
     assert e.value.code == C.RNG_ENOMEM
 
 
+def test_on_torch_current_stream_without_sync():
+    # Launched on torch's current stream, the output can feed torch ops with
+    # no explicit synchronisation in between.
+    n, T = 50_000, 20
+    g = rng.Generator(n, 8, compute_stream=torch.cuda.current_stream())
+    out = g.generate(T)
+    lo32 = (out.view(torch.int64) & 0xFFFFFFFF).sum(dim=1)   # queued right behind the kernel
+    got = lo32.cpu().numpy()
+    g.close()
+    want = (oracle.generate(n, 8, T) & np.uint64(0xFFFFFFFF)).astype(np.int64).sum(axis=1)
+    assert np.array_equal(got, want)
+
+
 def test_live_objects_balance():
     before = rng.live_objects()
     gs = [rng.Generator(100, k) for k in range(3)]
