@@ -18,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librng_gb300.so")
+EXAMPLE = os.path.join(BUILD, "rng_stdout")
+EXAMPLE_SRC = os.path.join(HERE, "examples", "rng_stdout.c")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,10 +44,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(EXAMPLE):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(EXAMPLE))
+    return all(os.path.getmtime(p) <= t for p in _deps() + [EXAMPLE_SRC])
 
 
 def _compile(src: str, nvcc: str, verbose_ptxas: bool) -> str:
@@ -78,6 +80,14 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    # The paper's example program as a plain C client of the library.
+    tmp = EXAMPLE + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-I", INCLUDE, EXAMPLE_SRC, "-o", tmp, "-L", BUILD, "-l:librng_gb300.so",
+           "-Wl,-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"example build failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, EXAMPLE)
     return LIB
 
 

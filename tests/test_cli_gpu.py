@@ -39,6 +39,19 @@ def test_cli_stdout_matches_oracle():
     assert b"Aggregate times by event" in r.stderr
 
 
+def test_c_example_program_matches_oracle():
+    # The paper's program as a plain C client of the library (built by build()).
+    from paper_1609_01257_gb300 import builder
+    n, T = 2000, 5
+    r = subprocess.run([builder.EXAMPLE, str(n), str(T), "7"], capture_output=True, timeout=300)
+    assert r.returncode == 0, r.stderr.decode()
+    got = np.frombuffer(r.stdout, dtype=np.uint64)
+    assert got.size == n * T
+    assert np.array_equal(got.reshape(T, n), oracle.generate(n, 7, T))
+    assert b"Time spent in device" in r.stderr
+    assert b"objects left alive" not in r.stderr
+
+
 def test_queue_chart_export_of_the_papers_run(tmp_path):
     # One 128 MiB row per device buffer: each iteration is one kernel on the
     # main queue and one read on the comms queue, the reads of one buffer
