@@ -399,7 +399,8 @@ def run_served(args):
     reqs = workloads.served_requests(duration_s=args.duration)
     offered = sum(r.nbytes for r in reqs)
     with rng.Server(hbm_budget_bytes=64 << 30, step_bytes=args.step_bytes,
-                    max_steps_in_flight=args.steps_in_flight, values_per_thread=args.server_vpt) as srv:
+                    max_steps_in_flight=args.steps_in_flight, values_per_thread=args.server_vpt,
+                    mode=args.server_mode) as srv:
         warm = workloads.served_requests(duration_s=0.5, seed_start=5, arrival_start=6, size_start=7)
         rng.run_load(srv, warm)
         res = rng.run_load(srv, reqs)
@@ -412,7 +413,7 @@ def run_served(args):
                 "wall_s": res.wall_s, "worst_submit_lag_ms": res.submit_lag_s * 1e3,
                 "steps": st["steps"], "peak_active": st["peak_active"],
                 "server": {"step_bytes": args.step_bytes, "steps_in_flight": args.steps_in_flight,
-                           "values_per_thread": args.server_vpt},
+                           "values_per_thread": args.server_vpt, "mode": args.server_mode},
                 "peak_bytes_in_use": st["peak_bytes_in_use"]})
     return 0
 
@@ -554,6 +555,7 @@ def main(argv=None):
     ap.add_argument("--step-bytes", type=int, default=2 << 30, help="served: output bytes per step")
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
+    ap.add_argument("--server-mode", type=int, default=1, help="served: 1 one unit per block, 2 persistent")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")

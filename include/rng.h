@@ -404,6 +404,8 @@ typedef struct rng_server_opts {
     uint32_t max_units_per_step;  /* work-table capacity per step; default 1<<20 */
     int32_t device;               /* -1 = current */
     void *stream;                 /* cudaStream_t; NULL = own stream */
+    uint32_t mode;                /* 1 (default) = one work unit per block,
+                                     2 = persistent blocks with a counter */
 } rng_server_opts;
 
 typedef struct rng_server_stats {

@@ -71,6 +71,7 @@ class RngServerOpts(ctypes.Structure):
         ("max_units_per_step", c_u32),
         ("device", c_i32),
         ("stream", c_vp),
+        ("mode", c_u32),
     ]
 
 

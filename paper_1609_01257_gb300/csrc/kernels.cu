@@ -292,48 +292,52 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
   }
 }
 
-// One work unit of the work-list kernel: one tile of streams of one chunk,
-// all rows of the chunk.
+// One work unit of the work-list kernel: `count` streams of one chunk from
+// s_begin, all rows of the chunk, processed one tile (kBlock * VPT streams)
+// at a time.  Units of instances with few rows span several tiles so that
+// units carry similar numbers of bytes.
 template <int VPT>
 __device__ __forceinline__ void process_unit(const BatchInstance *__restrict__ inst,
                                              const BatchUnit *__restrict__ units, uint32_t u) {
   const BatchUnit wu = units[u];
   const BatchInstance in = inst[wu.inst];
-  RowsLaunch a;
-  a.state = in.state;
-  a.out = in.out;
-  a.pitch = in.streams;
-  a.s_begin = wu.s_begin;
-  a.s_end = wu.s_begin + wu.count;
-  a.id_base = 0;
-  a.rows = in.rows;
-  a.key = in.key;
-  a.from_hash = in.from_hash;
-  a.write_state = in.write_state;
-  a.ring_rows = 0;
-  const uint64_t span = wu.count;
   const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
-  uint64_t *row = in.out + wu.s_begin;
-  // 16-byte stores for few values per thread on aligned rows; one streaming
-  // 8-byte store per value otherwise (the faster form once a thread holds six
-  // or more streams).
-  if (VPT % 2 == 0 && VPT < 6 && in.vec) {
-    constexpr int V2 = VPT >= 2 ? VPT : 2;
-    uint64_t st[V2];
-    load_tile<V2, 2>(st, a, 0, span);
-    if (span == tile_vals)
-      emit_rows<V2, 2, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
-    else
-      emit_rows<V2, 2, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
-    if (a.write_state) store_tile_state<V2, 2>(st, a.state, a, 0, span);
-  } else {
-    uint64_t st[VPT];
-    load_tile<VPT, 1>(st, a, 0, span);
-    if (span == tile_vals)
-      emit_rows<VPT, 1, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
-    else
-      emit_rows<VPT, 1, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
-    if (a.write_state) store_tile_state<VPT, 1>(st, a.state, a, 0, span);
+  for (uint64_t off = 0; off < wu.count; off += tile_vals) {
+    RowsLaunch a;
+    a.state = in.state;
+    a.out = in.out;
+    a.pitch = in.streams;
+    a.s_begin = wu.s_begin + off;
+    a.s_end = wu.s_begin + wu.count;
+    a.id_base = 0;
+    a.rows = in.rows;
+    a.key = in.key;
+    a.from_hash = in.from_hash;
+    a.write_state = in.write_state;
+    a.ring_rows = 0;
+    const uint64_t span = wu.count - off;
+    uint64_t *row = in.out + a.s_begin;
+    // 16-byte stores for few values per thread on aligned rows; one
+    // streaming 8-byte store per value otherwise (the faster form once a
+    // thread holds six or more streams).
+    if (VPT % 2 == 0 && VPT < 6 && in.vec) {
+      constexpr int V2 = VPT >= 2 ? VPT : 2;
+      uint64_t st[V2];
+      load_tile<V2, 2>(st, a, 0, span);
+      if (span >= tile_vals)
+        emit_rows<V2, 2, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
+      else
+        emit_rows<V2, 2, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
+      if (a.write_state) store_tile_state<V2, 2>(st, a.state, a, 0, span);
+    } else {
+      uint64_t st[VPT];
+      load_tile<VPT, 1>(st, a, 0, span);
+      if (span >= tile_vals)
+        emit_rows<VPT, 1, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
+      else
+        emit_rows<VPT, 1, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
+      if (a.write_state) store_tile_state<VPT, 1>(st, a.state, a, 0, span);
+    }
   }
 }
 

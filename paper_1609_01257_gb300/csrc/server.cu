@@ -194,11 +194,15 @@ struct rng_server {
                                     cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(ts.d_units, ts.h_units, n_units * sizeof(rngi::BatchUnit), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ts.d_counter, 0, sizeof(uint32_t), stream);
+    // Work distribution: one unit per block (hardware dispatch in table
+    // order), or persistent blocks taking units from a counter.
+    const bool per_block = opts.mode != 2;
+    if (e == cudaSuccess && !per_block) e = cudaMemsetAsync(ts.d_counter, 0, sizeof(uint32_t), stream);
     const uint64_t resident = uint64_t(sms) * grid_per_sm;
-    const uint32_t grid = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(resident, n_units)));
+    const uint32_t grid = per_block ? static_cast<uint32_t>(n_units)
+                                    : static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(resident, n_units)));
     if (e == cudaSuccess)
-      e = rngi::launch_batch(ts.d_inst, ts.d_units, static_cast<uint32_t>(n_units), ts.d_counter,
+      e = rngi::launch_batch(ts.d_inst, ts.d_units, static_cast<uint32_t>(n_units), per_block ? nullptr : ts.d_counter,
                              opts.values_per_thread, kBlock, grid, stream);
     if (e == cudaSuccess) e = cudaEventRecord(ts.done, stream);
     if (e != cudaSuccess) {
@@ -319,6 +323,7 @@ void rng_server_opts_default(rng_server_opts *o) {
   o->max_steps_in_flight = 2;
   o->values_per_thread = 8;
   o->max_units_per_step = 1u << 20;
+  o->mode = 1;
   o->device = -1;
   o->stream = nullptr;
 }
@@ -337,6 +342,7 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
   if (!rngi::batch_vpt_supported(o.values_per_thread))
     return rngi::fail(err, RNG_EINVAL,
                       "rng_server_create: values_per_thread must be one of 1, 2, 4, 6, 8, 12, 16, 24, 32");
+  if (o.mode < 1 || o.mode > 2) return rngi::fail(err, RNG_EINVAL, "rng_server_create: mode must be 1 or 2");
   if (o.max_active == 0 || o.max_steps_in_flight == 0 || o.step_bytes == 0 || o.max_units_per_step == 0 ||
       o.hbm_budget_bytes < kAlign)
     return rngi::fail(err, RNG_EINVAL, "rng_server_create: zero limit in options");

@@ -22,7 +22,8 @@ from . import _capi as C
 class Server:
     def __init__(self, *, hbm_budget_bytes: int = 64 << 30, max_active: int = 1024,
                  step_bytes: int = 2 << 30, max_steps_in_flight: int = 2, values_per_thread: int = 8,
-                 max_units_per_step: int = 1 << 20, stream=None, device: Optional[int] = None):
+                 max_units_per_step: int = 1 << 20, mode: int = 1, stream=None,
+                 device: Optional[int] = None):
         lib = C.load()
         o = C.RngServerOpts()
         lib.rng_server_opts_default(ctypes.byref(o))
@@ -32,6 +33,7 @@ class Server:
         o.max_steps_in_flight = max_steps_in_flight
         o.values_per_thread = values_per_thread
         o.max_units_per_step = max_units_per_step
+        o.mode = mode
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         if stream is None:
             stream = torch.cuda.Stream(device=self.device)

@@ -98,6 +98,33 @@ def test_stream_offset_is_a_column_block():
     assert np.array_equal(got, oracle.generate(n, 77, T, g0=off))
 
 
+def test_ids_up_to_the_32_bit_limit():
+    # The last ids a generator can own: stream_offset + streams == 2^32.
+    n = 1000
+    got = dev_gen(n, 5, 4, stream_offset=(1 << 32) - n)
+    assert np.array_equal(got, oracle.generate(n, 5, 4, g0=(1 << 32) - n))
+    with pytest.raises(rng.RngError):
+        rng.Generator(n, 5, stream_offset=(1 << 32) - n + 1)
+
+
+def test_maximum_stream_count():
+    # 2^32 streams (the id width): 2 iterations = 64 GiB of output plus a
+    # 32 GiB state array; sampled values one by one.
+    n, T, seed = 1 << 32, 2, 3
+    g = rng.Generator(n, seed)
+    out = g.generate(T)
+    g.sync()
+    o64 = out.view(torch.int64).view(-1)
+    rs = np.random.default_rng(4)
+    idx = [0, 1, n - 1, n, 2 * n - 1] + [int(i) for i in rs.integers(0, 2 * n, 40)]
+    vals = o64[torch.tensor(idx, device="cuda")].cpu().numpy().view(np.uint64)
+    del out, o64
+    g.close()
+    for k, v in zip(idx, vals):
+        i, gg = divmod(k, n)
+        assert int(v) == oracle.value(gg, seed, i), (i, gg)
+
+
 def test_generate_before_init_is_an_error():
     g = rng.Generator(10, 1, init=False)
     with pytest.raises(rng.RngError) as e:
