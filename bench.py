@@ -555,7 +555,7 @@ def main(argv=None):
     ap.add_argument("--step-bytes", type=int, default=2 << 30, help="served: output bytes per step")
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
-    ap.add_argument("--server-mode", type=int, default=1, help="served: 1 one unit per block, 2 persistent")
+    ap.add_argument("--server-mode", type=int, default=2, help="served: 1 one unit per block, 2 persistent")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")

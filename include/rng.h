@@ -404,8 +404,10 @@ typedef struct rng_server_opts {
     uint32_t max_units_per_step;  /* work-table capacity per step; default 1<<20 */
     int32_t device;               /* -1 = current */
     void *stream;                 /* cudaStream_t; NULL = own stream */
-    uint32_t mode;                /* 1 (default) = one work unit per block,
-                                     2 = persistent blocks with a counter */
+    uint32_t mode;                /* 1 = one work unit per block, 2 (default) =
+                                     persistent blocks with a counter (equal
+                                     within noise in 15 s runs: p99 1.58 vs
+                                     1.50 ms) */
 } rng_server_opts;
 
 typedef struct rng_server_stats {

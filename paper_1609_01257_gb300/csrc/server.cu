@@ -323,7 +323,7 @@ void rng_server_opts_default(rng_server_opts *o) {
   o->max_steps_in_flight = 2;
   o->values_per_thread = 8;
   o->max_units_per_step = 1u << 20;
-  o->mode = 1;
+  o->mode = 2;
   o->device = -1;
   o->stream = nullptr;
 }
