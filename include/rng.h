@@ -222,6 +222,11 @@ int rng_position(const rng_gen *g, uint64_t *position);
 int rng_streams(const rng_gen *g, uint64_t *streams);
 /* Copies the current states (s_p of each stream) to host memory. Blocks. */
 int rng_get_state(rng_gen *g, uint64_t *host_states, rng_err **err);
+/* Checkpoint restore: loads one state per stream from host memory and sets
+ * the position to `position` (the iteration those states emit next), e.g.
+ * states saved with rng_get_state.  Leaves the generator initialised.
+ * Blocks until the copy is done. */
+int rng_set_state(rng_gen *g, const uint64_t *host_states, uint64_t position, rng_err **err);
 /* Waits for all work the generator has queued. */
 int rng_sync(rng_gen *g, rng_err **err);
 /* The compute stream (cudaStream_t) the generator launches on. */

@@ -103,6 +103,7 @@ SIGNATURES = {
     "rng_position": ([c_vp, P_u64], c_int),
     "rng_streams": ([c_vp, P_u64], c_int),
     "rng_get_state": ([c_vp, c_vp, P_err], c_int),
+    "rng_set_state": ([c_vp, c_vp, c_u64, P_err], c_int),
     "rng_sync": ([c_vp, P_err], c_int),
     "rng_compute_stream": ([c_vp], c_vp),
     "rng_launch_config": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)], c_int),

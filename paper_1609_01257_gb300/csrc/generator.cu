@@ -788,6 +788,20 @@ int rng_get_state(rng_gen *g, uint64_t *host_states, rng_err **err) {
   return rngi::cuda_fail(err, st, "rng_get_state copy");
 }
 
+int rng_set_state(rng_gen *g, const uint64_t *host_states, uint64_t position, rng_err **err) {
+  int rc = check_gen(g, err, "rng_set_state");
+  if (rc) return rc;
+  if (!host_states) return rngi::fail(err, RNG_EINVAL, "rng_set_state: NULL states");
+  cudaError_t st = cudaMemcpyAsync(g->d_state, host_states, g->n * 8, cudaMemcpyHostToDevice, g->compute);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(g->compute);
+  rc = rngi::cuda_fail(err, st, "rng_set_state copy");
+  if (rc) return rc;
+  g->materialized = true;
+  g->initialized = true;
+  g->pos = position;
+  return RNG_OK;
+}
+
 int rng_sync(rng_gen *g, rng_err **err) {
   int rc = check_gen(g, err, "rng_sync");
   if (rc) return rc;

@@ -215,6 +215,13 @@ class Generator:
         C.check(self._lib.rng_get_state, self._h, ctypes.c_void_p(out.ctypes.data))
         return out
 
+    def set_state(self, states: np.ndarray, position: int):
+        """Restore a checkpoint: per-stream states (as from ``state()``) and
+        the iteration they emit next."""
+        states = np.ascontiguousarray(states, dtype=np.uint64)
+        assert states.size == self.streams
+        C.check(self._lib.rng_set_state, self._h, ctypes.c_void_p(states.ctypes.data), position)
+
     def sync(self):
         C.check(self._lib.rng_sync, self._h)
 

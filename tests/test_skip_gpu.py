@@ -58,3 +58,20 @@ def test_full_period_returns_to_start():
     again = g.generate(1).cpu().numpy()
     g.close()
     assert np.array_equal(first, again)
+
+
+def test_checkpoint_and_resume():
+    # Save (states, position) mid-run, restore into a new generator, continue.
+    n = 5000
+    a = rng.Generator(n, 44)
+    a.generate(7)
+    states, pos = a.state(), a.position
+    rest_a = a.generate(5).cpu().numpy()
+    a.close()
+    b = rng.Generator(n, 44, init=False)
+    b.set_state(states, pos)
+    rest_b = b.generate(5).cpu().numpy()
+    assert b.position == 12
+    b.close()
+    assert np.array_equal(rest_a, rest_b)
+    assert np.array_equal(rest_b, oracle.generate(n, 44, 5, p0=7))
