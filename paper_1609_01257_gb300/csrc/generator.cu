@@ -127,6 +127,40 @@ int profile_restart(rng_gen *g, rng_err **err) {
 
 constexpr uint32_t kMaxJumpMatrices = 64;
 
+// Prepares a banded launch of `a` with `br` rows per band: the second state
+// array (final states go there; the generator switches to it after the
+// launch) and the GF(2) jump table on the device.
+int setup_bands(rng_gen *g, rngi::RowsLaunch &a, uint64_t br, bool *swap, rng_err **err) {
+  const uint64_t bands = (a.rows + br - 1) / br;
+  uint32_t count = 0;
+  while ((uint64_t(1) << count) < bands) ++count;  // bits of band indices 0 .. bands-1
+  if (count == 0) count = 1;
+  int rc = RNG_OK;
+  if (!g->d_state2)
+    rc = rngi::cuda_fail(err, cudaMalloc(&g->d_state2, g->n * 8), "cudaMalloc(second state array)");
+  if (!rc && !g->d_jump)
+    rc = rngi::cuda_fail(err, cudaMalloc(&g->d_jump, kMaxJumpMatrices * 64 * 8), "cudaMalloc(jump table)");
+  if (rc) return rc;
+  if (g->jump_rows != br || g->jump_count < count) {
+    std::vector<uint64_t> cols(size_t(count) * 64);
+    rngi::jump_table(br, count, cols.data());
+    // Pageable source: the call returns once the source has been read.
+    rc = rngi::cuda_fail(err, cudaMemcpyAsync(g->d_jump, cols.data(), cols.size() * 8, cudaMemcpyHostToDevice,
+                                              g->compute),
+                         "jump table upload");
+    if (rc) return rc;
+    g->jump_rows = br;
+    g->jump_count = count;
+  }
+  a.band_rows = br;
+  a.jump = g->d_jump;
+  if (a.write_state) {
+    a.state_out = g->d_state2;
+    *swap = true;
+  }
+  return RNG_OK;
+}
+
 // Launches the row kernel for `a`.  When the launch covers every stream but
 // has too few tiles to fill the GPU, its rows are split into bands run by
 // separate blocks: each band's blocks jump their states ahead over GF(2),
@@ -140,33 +174,8 @@ int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh
   if (!a.ring_rows && a.out && a.s_begin == 0 && a.s_end == g->n) {
     const uint64_t br = rngi::choose_band_rows(g->n, a.rows, sh, g->device);
     if (br) {
-      const uint64_t bands = (a.rows + br - 1) / br;
-      uint32_t count = 0;
-      while ((uint64_t(1) << count) < bands) ++count;  // bits of band indices 0 .. bands-1
-      if (count == 0) count = 1;
-      int rc = RNG_OK;
-      if (!g->d_state2)
-        rc = rngi::cuda_fail(err, cudaMalloc(&g->d_state2, g->n * 8), "cudaMalloc(second state array)");
-      if (!rc && !g->d_jump)
-        rc = rngi::cuda_fail(err, cudaMalloc(&g->d_jump, kMaxJumpMatrices * 64 * 8), "cudaMalloc(jump table)");
+      int rc = setup_bands(g, a, br, &swap, err);
       if (rc) return rc;
-      if (g->jump_rows != br || g->jump_count < count) {
-        std::vector<uint64_t> cols(size_t(count) * 64);
-        rngi::jump_table(br, count, cols.data());
-        // Pageable source: the call returns once the source has been read.
-        rc = rngi::cuda_fail(err, cudaMemcpyAsync(g->d_jump, cols.data(), cols.size() * 8, cudaMemcpyHostToDevice,
-                                                  g->compute),
-                             "jump table upload");
-        if (rc) return rc;
-        g->jump_rows = br;
-        g->jump_count = count;
-      }
-      a.band_rows = br;
-      a.jump = g->d_jump;
-      if (a.write_state) {
-        a.state_out = g->d_state2;
-        swap = true;
-      }
     }
   }
   long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
@@ -735,12 +744,25 @@ int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev
   a.key = g->key;
   a.from_hash = !g->materialized;
   a.write_state = 1;
-  long op = op_begin(g, "CHECKSUM_KERNEL", kQueueMain, g->compute);
+  a.state_out = a.state;
   const uint32_t v = g->opts.values_per_thread;
-  st = rngi::launch_checksum(a, (v && (v & (v - 1)) == 0) ? v : 0, row_xor_dev, row_sum_dev, g->compute);
+  const uint32_t vpt = rngi::checksum_vpt(g->n, (v && (v & (v - 1)) == 0 && v <= 64) ? v : 0, g->device);
+  // Few tiles, many rows: bands, as for the row kernel.
+  rngi::LaunchShape sh{};
+  sh.vpt = vpt;
+  sh.block = rngi::kGenBlock;
+  bool swap = false;
+  const uint64_t br = rngi::choose_band_rows(g->n, iterations, sh, g->device, true);
+  if (br) {
+    rc = setup_bands(g, a, br, &swap, err);
+    if (rc) return rc;
+  }
+  long op = op_begin(g, "CHECKSUM_KERNEL", kQueueMain, g->compute);
+  st = rngi::launch_checksum(a, vpt, row_xor_dev, row_sum_dev, g->compute);
   op_end(g, op, g->compute);
   rc = rngi::cuda_fail(err, st, "checksum kernel launch");
   if (rc) return rc;
+  if (swap) std::swap(g->d_state, g->d_state2);
   g->materialized = true;
   g->pos += iterations;
   return RNG_OK;

@@ -18,7 +18,7 @@ constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
 // banded: the variant that splits rows into bands (few values per thread
 // only; store policy is always streaming there).
 const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded = false);
-const void *checksum_kernel_fn(uint32_t vpt);
+const void *checksum_kernel_fn(uint32_t vpt, bool banded = false);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *init_kernel_fn();
 const void *jump_kernel_fn();
@@ -77,8 +77,11 @@ cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t 
 // from_hash), where M is the update's matrix over GF(2).
 cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key, int from_hash,
                         uint64_t k, cudaStream_t st);
-// Generate-and-checksum launch; vpt = 0 picks values per thread (a power of
-// two up to 64 otherwise).
+// Values per thread of a generate-and-checksum launch over `span` streams
+// (vpt = 0: choose; else a power of two up to 64).
+uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device);
+// Generate-and-checksum launch with `vpt` values per thread; a.band_rows != 0
+// selects the banded variant (a.jump, a.state_out as for the row kernel).
 cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,
                             cudaStream_t st);
 int device_sm_count(int device);
@@ -109,7 +112,9 @@ cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint
 int batch_blocks_per_sm(uint32_t vpt, uint32_t block);
 // Rows per band when a launch should split its rows across blocks (few
 // streams, many rows: too few tiles to fill the GPU); 0 for no split.
-uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device);
+// `checksum`: for the generate-and-checksum kernel instead of the row kernel.
+uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device,
+                          bool checksum = false);
 // Host-side GF(2) tables for banded launches: writes `count` matrices
 // M^(band_rows * 2^b), b = 0 .. count-1, as 64 column words each.
 void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols);

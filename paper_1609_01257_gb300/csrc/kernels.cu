@@ -246,7 +246,10 @@ __device__ __forceinline__ void warp_xor_sum(uint64_t &x, uint64_t &s) {
 // Generate-and-checksum: per row, XOR and sum of all values of the launch's
 // stream range, reduced per warp, then per block (double-buffered shared
 // slots, one barrier per row), then one atomic pair per block and row.
-template <int VPT>
+// Banded (BANDED = true): work units are (tile, band of band_rows rows), each
+// unit jumping its states ahead to its band over GF(2) as in the row kernel;
+// final states go to state_out (from the last band).
+template <int VPT, bool BANDED>
 __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
                                                        unsigned long long *row_xor,
                                                        unsigned long long *row_sum) {
@@ -256,11 +259,18 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
   const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int n_warps = kBlock / 32;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  const uint64_t band_rows = BANDED ? a.band_rows : (a.rows ? a.rows : 1);
+  const uint64_t n_bands = BANDED ? (a.rows + band_rows - 1) / band_rows : 1;
+  for (uint64_t w = blockIdx.x; w < n_tiles * n_bands; w += gridDim.x) {
+    const uint64_t tile = w % n_tiles;
+    const uint64_t band = BANDED ? w / n_tiles : 0;
     const uint64_t rel0 = tile * tile_vals;
     uint64_t st[VPT];
     load_tile<VPT, 1>(st, a, rel0, span);
-    for (uint64_t r = 0; r < a.rows; ++r) {
+    if (BANDED && band) jump_states<VPT>(st, a.jump, band);
+    const uint64_t r0 = band * band_rows;
+    const uint64_t rows = BANDED ? (a.rows - r0 < band_rows ? a.rows - r0 : band_rows) : a.rows;
+    for (uint64_t r = 0; r < rows; ++r) {
       uint64_t x = 0, s = 0;
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
@@ -280,14 +290,15 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
         uint64_t bs = lane < n_warps ? ss[buf][lane] : 0;
         warp_xor_sum(bx, bs);
         if (lane == 0) {
-          atomicXor(row_xor + r, static_cast<unsigned long long>(bx));
-          atomicAdd(row_sum + r, static_cast<unsigned long long>(bs));
+          atomicXor(row_xor + r0 + r, static_cast<unsigned long long>(bx));
+          atomicAdd(row_sum + r0 + r, static_cast<unsigned long long>(bs));
         }
       }
     }
     // Values past the end of the range were loaded as 0 and advance to 0,
     // so they add nothing; the states of real streams are written back.
-    if (a.write_state) store_tile_state<VPT, 1>(st, a.state, a, rel0, span);
+    if (a.write_state && band == n_bands - 1)
+      store_tile_state<VPT, 1>(st, BANDED ? a.state_out : a.state, a, rel0, span);
     __syncthreads();
   }
 }
@@ -438,17 +449,22 @@ const void *select_rows(uint32_t vpt, int width, int policy, uint32_t block = kB
   }
 }
 
-const void *select_checksum(uint32_t vpt) {
+template <bool BANDED>
+const void *select_checksum_t(uint32_t vpt) {
   switch (vpt) {
-    case 1: return reinterpret_cast<const void *>(&checksum_kernel<1>);
-    case 2: return reinterpret_cast<const void *>(&checksum_kernel<2>);
-    case 4: return reinterpret_cast<const void *>(&checksum_kernel<4>);
-    case 8: return reinterpret_cast<const void *>(&checksum_kernel<8>);
-    case 16: return reinterpret_cast<const void *>(&checksum_kernel<16>);
-    case 32: return reinterpret_cast<const void *>(&checksum_kernel<32>);
-    case 64: return reinterpret_cast<const void *>(&checksum_kernel<64>);
+    case 1: return reinterpret_cast<const void *>(&checksum_kernel<1, BANDED>);
+    case 2: return reinterpret_cast<const void *>(&checksum_kernel<2, BANDED>);
+    case 4: return reinterpret_cast<const void *>(&checksum_kernel<4, BANDED>);
+    case 8: return reinterpret_cast<const void *>(&checksum_kernel<8, BANDED>);
+    case 16: return reinterpret_cast<const void *>(&checksum_kernel<16, BANDED>);
+    case 32: return reinterpret_cast<const void *>(&checksum_kernel<32, BANDED>);
+    case 64: return reinterpret_cast<const void *>(&checksum_kernel<64, BANDED>);
     default: return nullptr;
   }
+}
+
+const void *select_checksum(uint32_t vpt, bool banded) {
+  return banded ? select_checksum_t<true>(vpt) : select_checksum_t<false>(vpt);
 }
 
 const void *select_batch(uint32_t vpt) {
@@ -474,7 +490,7 @@ const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, 
   if (banded) return block == kBlock ? select_rows_banded(vpt, width) : nullptr;
   return select_rows(vpt, width, policy, block);
 }
-const void *checksum_kernel_fn(uint32_t vpt) { return select_checksum(vpt); }
+const void *checksum_kernel_fn(uint32_t vpt, bool banded) { return select_checksum(vpt, banded); }
 const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }
 const void *init_kernel_fn() { return reinterpret_cast<const void *>(&init_kernel); }
 const void *jump_kernel_fn() { return reinterpret_cast<const void *>(&jump_kernel); }

@@ -172,13 +172,15 @@ void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols) {
 // 2^16 streams ran at 7.37 TB/s, three bands of them at 6.25); then about
 // two (tile, band) units per SM (16 tiles of 4096 streams: 19 bands 6.6 TB/s,
 // 10 bands 4.7 TB/s).
-uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device) {
+uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device, bool checksum) {
   const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
   const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
   const uint64_t target = 2 * sms;            // units wanted in flight
   const uint64_t min_band = 128;              // rows per band: amortises the jump
   if (tiles * 2 >= sms || rows < 2 * min_band) return 0;
-  if (!rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true)) return 0;  // no banded variant
+  const bool have = checksum ? checksum_kernel_fn(sh.vpt, true) != nullptr
+                             : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true) != nullptr;
+  if (!have) return 0;  // no banded variant of this shape
   uint64_t bands = (target + tiles - 1) / tiles;
   if (bands > rows / min_band) bands = rows / min_band;
   if (bands < 2) return 0;
@@ -199,28 +201,31 @@ cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t 
   return e;
 }
 
+uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device) {
+  (void)device;
+  if (vpt) return vpt;
+  // 16 values per thread amortise the per-row reductions best (2^22 and 2^26
+  // streams: 1.72e12 values/s at 16, 1.38e12 at 8); runs with few tiles are
+  // banded to fill the GPU (2^18 streams: 1.21e12 banded at 16 vs 0.83e12
+  // unbanded at 8).  Smaller values only when one tile would be mostly empty.
+  for (uint32_t v = 16; v >= 2; v /= 2)
+    if (span >= uint64_t(kGenBlock) * v) return v;
+  return 1;
+}
+
 cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,
                             cudaStream_t st) {
   const uint64_t span = a.s_end - a.s_begin;
   int dev = 0;
   cudaGetDevice(&dev);
   const int sms = device_sm_count(dev);
-  if (vpt == 0) {
-    // Up to 16 values per thread to amortise the per-row reductions, while
-    // keeping at least one tile per two SMs (measured: 2^22 and 2^26 streams
-    // fastest at 16; 2^18 at 8, 1.5x the rate of 1).
-    vpt = 1;
-    for (uint32_t v = 16; v >= 2; v /= 2)
-      if (span / (uint64_t(kGenBlock) * v) >= uint64_t(sms) / 2) {
-        vpt = v;
-        break;
-      }
-  }
-  const void *fn = checksum_kernel_fn(vpt);
+  if (a.band_rows && (!a.jump || (a.write_state && a.state_out == a.state))) return cudaErrorInvalidValue;
+  const void *fn = checksum_kernel_fn(vpt, a.band_rows != 0);
   if (!fn) return cudaErrorInvalidValue;
   const uint64_t tiles = (span + uint64_t(kGenBlock) * vpt - 1) / (uint64_t(kGenBlock) * vpt);
+  const uint64_t units = a.band_rows ? tiles * ((a.rows + a.band_rows - 1) / a.band_rows) : tiles;
   const uint64_t resident = uint64_t(sms) * occupancy(fn, kGenBlock);
-  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(tiles, resident)));
+  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(units, resident)));
   RowsLaunch args = a;
   unsigned long long *rx = reinterpret_cast<unsigned long long *>(row_xor);
   unsigned long long *rs = reinterpret_cast<unsigned long long *>(row_sum);

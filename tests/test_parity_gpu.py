@@ -328,6 +328,26 @@ def test_few_streams_many_rows_split_into_bands(n, T):
     assert np.array_equal(b, want[T:])
 
 
+@pytest.mark.parametrize("vpt", [24, 32, 64])
+def test_few_streams_many_rows_shapes_without_banded_variant(vpt):
+    # Shapes compiled without a banded variant run unbanded.
+    n, T = 3000, 600
+    got = dev_gen(n, 29, T, values_per_thread=vpt)
+    assert np.array_equal(got, oracle.generate(n, 29, T))
+
+
+@pytest.mark.parametrize("n,T", [(1, 3000), (100, 1000), (4097, 700), (1 << 16, 300)])
+def test_checksum_mode_banded(n, T):
+    g = rng.Generator(n, 31)
+    rx, rs = g.generate_checksum(T)
+    g.sync()
+    tail = g.generate(2).cpu().numpy()
+    g.close()
+    wx, ws, _ = oracle.row_checksums(n, 31, T)
+    assert np.array_equal(rx.cpu().numpy(), wx) and np.array_equal(rs.cpu().numpy(), ws)
+    assert np.array_equal(tail, oracle.generate(n, 31, 2, p0=T))
+
+
 @pytest.mark.parametrize("host_path", [1, 2])
 def test_few_streams_many_rows_to_host(host_path):
     n, T = 1000, 3000
