@@ -8,6 +8,7 @@ reports latency percentiles and throughput.
 from __future__ import annotations
 
 import ctypes
+import gc
 import threading
 import time
 from dataclasses import dataclass, field
@@ -145,6 +146,8 @@ def run_load(server: Server, requests: Sequence, *, time_scale: float = 1.0,
             errors.append(e)
 
     th = threading.Thread(target=collector, daemon=True)
+    gc_was_enabled = gc.isenabled()
+    gc.disable()  # a collection pause would delay submissions behind their arrival times
     t0 = time.perf_counter()
     th.start()
     for i, r in enumerate(requests):
@@ -164,6 +167,8 @@ def run_load(server: Server, requests: Sequence, *, time_scale: float = 1.0,
             break
     th.join(timeout_s)
     res.wall_s = time.perf_counter() - t0
+    if gc_was_enabled:
+        gc.enable()
     if errors:
         raise errors[0]
     if th.is_alive():
