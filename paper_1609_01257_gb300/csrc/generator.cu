@@ -93,6 +93,20 @@ cudaError_t next_event(rng_gen *g, size_t *idx) {
   return cudaSuccess;
 }
 
+// Creates the events `ops` more profiled ops will need, so that no event is
+// created inside a pipelined loop (creation blocks the enqueuing thread long
+// enough to open gaps between copies).
+void reserve_events(rng_gen *g, size_t ops) {
+  if (!g->opts.profiling) return;
+  const size_t room = kMaxOps > g->ops.size() ? kMaxOps - g->ops.size() : 0;
+  const size_t want = g->ev_used + 2 * std::min(ops, room);
+  while (g->evpool.size() < want) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    g->evpool.push_back(e);
+  }
+}
+
 // Records the start event of an op on `s`; returns the op slot or -1 when
 // profiling is off or the op log is full.
 long op_begin(rng_gen *g, const char *name, const char *queue, cudaStream_t s) {
@@ -341,6 +355,7 @@ int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn s
   int rc = ensure_buffers(g, staged, err);
   if (rc) return rc;
   const std::vector<Chunk> chunks = plan_chunks(g->n, T, g->buf_bytes);
+  reserve_events(g, 2 * chunks.size());  // one kernel and one read per chunk
   const bool hash_first_rows = !g->materialized;
   const uint64_t first_it = g->pos;
   g->initialized = false;  // re-armed only if the whole run succeeds
