@@ -187,9 +187,9 @@ struct rng_server {
       if (r->issued == r->iters) step.finishing.push_back(r->ticket);
     }
     if (n_inst == 0) return false;  // a single request needs more units than a step holds
-    std::stable_sort(ts.h_units, ts.h_units + n_units, [&](const rngi::BatchUnit &a, const rngi::BatchUnit &b) {
-      return uint64_t(a.count) * ts.h_inst[a.inst].rows > uint64_t(b.count) * ts.h_inst[b.inst].rows;
-    });
+    // Units stay in request order, each request's tiles together: blocks
+    // running at the same time write neighbouring parts of one output (as in
+    // the batched form, where this beat sorting all units by size).
     cudaError_t e = cudaMemcpyAsync(ts.d_inst, ts.h_inst, n_inst * sizeof(rngi::BatchInstance),
                                     cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
