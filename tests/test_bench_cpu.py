@@ -32,3 +32,16 @@ def test_peaks_file_is_read():
     assert peaks["hbm_gbs"] > 0
     if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
         assert src == "measured"
+
+
+def test_reference_arm_prints_one_json_line(capsys):
+    # The reference arm times the CPU oracle; it needs no GPU.
+    rc = bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3", "--reference-rows", "1"])
+    assert rc == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    import json
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
