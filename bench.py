@@ -351,9 +351,10 @@ def run_batched(args):
     import paper_1609_01257_gb300 as rng
     import workloads
 
-    inst = workloads.batched_instances()
+    inst = workloads.batched_instances(cap_bytes=int(args.batch_cap_gib * GIB))
     total = sum(i.nbytes for i in inst)
-    b = rng.Batch([i.streams for i in inst], [i.iterations for i in inst], [i.seed for i in inst])
+    b = rng.Batch([i.streams for i in inst], [i.iterations for i in inst], [i.seed for i in inst],
+                  values_per_thread=args.batch_vpt, mode=args.batch_mode)
     cfg = b.config()
     s = b.stream
     for _ in range(args.warmup):
@@ -389,7 +390,7 @@ def run_batched(args):
         g.close()
     b.close()
     _json_line({"workload": "batched: 512 instances, streams log-uniform [2^8, 2^20], iterations log-uniform "
-                            "[1, 4096] capped at 8 GiB, seeds splitmix64 from 7",
+                            f"[1, 4096] capped at {args.batch_cap_gib:g} GiB, seeds splitmix64 from 7",
                 "bytes_per_step": total, "batched_GBps": total / batched_s / 1e9, "batched_ms": batched_s * 1e3,
                 "plain_GBps": total / plain_s / 1e9, "plain_ms": plain_s * 1e3, "tuned": cfg,
                 "steps": args.steps, "warmup": args.warmup})
@@ -558,6 +559,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart"], default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
+    ap.add_argument("--batch-cap-gib", type=float, default=8.0, help="batched: total output cap")
+    ap.add_argument("--batch-vpt", type=int, default=0, help="batched: values per thread (0 = autotune)")
+    ap.add_argument("--batch-mode", type=int, default=0, help="batched: 0 autotune, 1 per block, 2 persistent")
     ap.add_argument("--step-bytes", type=int, default=2 << 30, help="served: output bytes per step")
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
