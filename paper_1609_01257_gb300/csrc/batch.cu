@@ -1,13 +1,14 @@
 // Batched form: many independent generator instances (each its own stream
 // count, iteration count and seed, each starting at iteration 0) produced by
-// one persistent kernel launch captured in a CUDA graph.
+// one kernel launch captured in a CUDA graph.
 //
 // Work is cut into units of one tile (256 threads x values-per-thread
-// streams) of one instance, with all of that instance's iterations.  Units are
-// ordered by decreasing output bytes and handed out through a device counter,
-// so the longest units start first and blocks that finish early take the
-// short ones.  The autotuner times the graph for each values-per-thread
-// candidate and keeps the fastest; every candidate writes the same bytes.
+// streams) of one instance, with all of that instance's iterations; each
+// unit is a self-contained 64-byte record.  Units run either one per block
+// (the hardware dispatches blocks in table order) or on persistent blocks
+// that take them from a device counter.  The autotuner times the graph for
+// each values-per-thread and distribution candidate and keeps the fastest;
+// every candidate writes the same bytes.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -23,8 +24,7 @@ struct rng_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<rngi::BatchInstance> inst;
-  rngi::BatchInstance *d_inst = nullptr;
-  rngi::BatchUnit *d_units = nullptr;
+  rngi::BatchWork *d_work = nullptr;
   size_t units_cap = 0;
   uint32_t *d_counter = nullptr;
   uint32_t n_units = 0;
@@ -60,32 +60,41 @@ int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
     return b->inst[x].streams * b->inst[x].rows > b->inst[y].streams * b->inst[y].rows;
   });
-  std::vector<rngi::BatchUnit> units;
-  for (uint32_t k : order)
-    for (uint64_t s = 0; s < b->inst[k].streams; s += tile) {
-      const uint64_t c = std::min<uint64_t>(tile, b->inst[k].streams - s);
-      units.push_back({k, static_cast<uint32_t>(c), s});
+  std::vector<rngi::BatchWork> units;
+  for (uint32_t k : order) {
+    const rngi::BatchInstance &in = b->inst[k];
+    for (uint64_t s = 0; s < in.streams; s += tile) {
+      rngi::BatchWork w{};
+      w.out = in.out;
+      w.streams = in.streams;
+      w.rows = in.rows;
+      w.s_begin = s;
+      w.count = static_cast<uint32_t>(std::min<uint64_t>(tile, in.streams - s));
+      w.key = in.key;
+      w.vec = in.vec;
+      units.push_back(w);
     }
+  }
   if (units.size() > 0xffffffffull) return rngi::fail(err, RNG_EINVAL, "rng_batch: too many work units");
   if (units.size() > b->units_cap) {
-    cudaFree(b->d_units);
-    b->d_units = nullptr;
-    int rc = rngi::cuda_fail(err, cudaMalloc(&b->d_units, units.size() * sizeof(rngi::BatchUnit)),
-                             "cudaMalloc(batch units)");
+    cudaFree(b->d_work);
+    b->d_work = nullptr;
+    int rc = rngi::cuda_fail(err, cudaMalloc(&b->d_work, units.size() * sizeof(rngi::BatchWork)),
+                             "cudaMalloc(batch work table)");
     if (rc) return rc;
     b->units_cap = units.size();
   }
   int rc = rngi::cuda_fail(err,
-                           cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(rngi::BatchUnit),
+                           cudaMemcpyAsync(b->d_work, units.data(), units.size() * sizeof(rngi::BatchWork),
                                            cudaMemcpyHostToDevice, b->stream),
-                           "cudaMemcpy(batch units)");
+                           "cudaMemcpy(batch work table)");
   if (rc) return rc;
   rc = rngi::cuda_fail(err, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
   if (rc) return rc;
   b->n_units = static_cast<uint32_t>(units.size());
   b->vpt = vpt;
   b->block = kBlock;
-  const int per_sm = rngi::batch_blocks_per_sm(vpt, kBlock);
+  const int per_sm = rngi::batch_work_blocks_per_sm(vpt);
   const uint64_t resident = uint64_t(rngi::device_sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
   b->per_block = per_block;
   b->grid = per_block ? b->n_units
@@ -95,8 +104,8 @@ int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
   cudaError_t st = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (st == cudaSuccess) {
     cudaError_t s1 = per_block ? cudaSuccess : cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), b->stream);
-    cudaError_t s2 = rngi::launch_batch(b->d_inst, b->d_units, b->n_units, per_block ? nullptr : b->d_counter,
-                                        vpt, kBlock, b->grid, b->stream);
+    cudaError_t s2 = rngi::launch_batch_work(b->d_work, b->n_units, per_block ? nullptr : b->d_counter, vpt,
+                                             b->grid, b->stream);
     st = cudaStreamEndCapture(b->stream, &b->graph);
     if (st == cudaSuccess) st = s1 != cudaSuccess ? s1 : s2;
   }
@@ -183,12 +192,7 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
     b->own_stream = rc == RNG_OK;
   }
-  if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&b->d_inst, count * sizeof(rngi::BatchInstance)), "cudaMalloc(batch)");
   if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&b->d_counter, sizeof(uint32_t)), "cudaMalloc(batch counter)");
-  if (!rc)
-    rc = rngi::cuda_fail(err, cudaMemcpyAsync(b->d_inst, b->inst.data(), count * sizeof(rngi::BatchInstance),
-                                              cudaMemcpyHostToDevice, b->stream),
-                         "cudaMemcpy(batch)");
   if (!rc && v) rc = prepare(b, v, o.mode == 1, err);
   if (!rc && !v) {
     // Autotune: time each candidate's graph and keep the fastest.
@@ -262,8 +266,7 @@ void rng_batch_destroy(rng_batch *b) {
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
-  cudaFree(b->d_inst);
-  cudaFree(b->d_units);
+  cudaFree(b->d_work);
   cudaFree(b->d_counter);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -20,6 +20,7 @@ constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
 const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded = false);
 const void *checksum_kernel_fn(uint32_t vpt, bool banded = false);
 const void *worklist_kernel_fn(uint32_t vpt);
+const void *batch_work_kernel_fn(uint32_t vpt);
 const void *init_kernel_fn();
 const void *jump_kernel_fn();
 
@@ -106,6 +107,26 @@ struct BatchUnit {
   uint32_t count;   // streams in this unit (<= tile)
   uint64_t s_begin;
 };
+// Self-contained work unit of the batched form: the instance's fields travel
+// with the unit, so a block needs one 64-byte load (no dependent second load)
+// before it can start.
+struct BatchWork {
+  uint64_t *out;      // instance output (row pitch = streams)
+  uint64_t streams;
+  uint64_t rows;
+  uint64_t s_begin;   // first stream of the unit
+  uint32_t count;     // streams in the unit (<= one tile)
+  uint32_t key;
+  uint32_t vec;       // rows 16-byte aligned
+  uint32_t pad[5];
+};
+static_assert(sizeof(BatchWork) == 64, "BatchWork is one 64-byte record");
+// Batched-form launch over `n` self-contained units (from the hash; no state):
+// one unit per block when counter == nullptr, else persistent blocks taking
+// units from the counter.
+cudaError_t launch_batch_work(const BatchWork *work, uint32_t n, uint32_t *counter, uint32_t vpt, uint32_t grid,
+                              cudaStream_t st);
+int batch_work_blocks_per_sm(uint32_t vpt);
 cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint32_t n_units,
                          uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
                          cudaStream_t st);

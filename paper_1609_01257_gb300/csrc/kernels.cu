@@ -376,6 +376,80 @@ __global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *_
   }
 }
 
+// Batched form over self-contained units (see BatchWork): every unit starts
+// from the id hash and writes all rows of one tile of one instance.
+template <int VPT>
+__device__ __forceinline__ void process_work(const BatchWork &w) {
+  RowsLaunch a;
+  a.state = nullptr;
+  a.out = w.out;
+  a.pitch = w.streams;
+  a.s_begin = w.s_begin;
+  a.s_end = w.s_begin + w.count;
+  a.id_base = 0;
+  a.rows = w.rows;
+  a.key = w.key;
+  a.from_hash = 1;
+  a.write_state = 0;
+  a.ring_rows = 0;
+  const uint64_t span = w.count;
+  const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  uint64_t *row = w.out + w.s_begin;
+  if (VPT % 2 == 0 && VPT < 6 && w.vec) {
+    constexpr int V2 = VPT >= 2 ? VPT : 2;
+    uint64_t st[V2];
+    load_tile<V2, 2>(st, a, 0, span);
+    if (span >= tile_vals)
+      emit_rows<V2, 2, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
+    else
+      emit_rows<V2, 2, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
+  } else {
+    uint64_t st[VPT];
+    load_tile<VPT, 1>(st, a, 0, span);
+    if (span >= tile_vals)
+      emit_rows<VPT, 1, kPolicyStreaming, false>(st, row, a.pitch, a.rows, 0, span);
+    else
+      emit_rows<VPT, 1, kPolicyStreaming, true>(st, row, a.pitch, a.rows, 0, span);
+  }
+}
+
+template <int VPT>
+__global__ void __launch_bounds__(kBlock) batch_work_kernel(const BatchWork *__restrict__ work, uint32_t n,
+                                                            uint32_t *counter) {
+  if (counter == nullptr) {
+    if (blockIdx.x < n) {
+      const BatchWork w = work[blockIdx.x];
+      process_work<VPT>(w);
+    }
+    return;
+  }
+  __shared__ uint32_t s_unit;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t u = s_unit;
+    __syncthreads();
+    if (u >= n) return;
+    const BatchWork w = work[u];
+    process_work<VPT>(w);
+  }
+}
+
+const void *select_batch_work(uint32_t vpt) {
+  switch (vpt) {
+    case 1: return reinterpret_cast<const void *>(&batch_work_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&batch_work_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&batch_work_kernel<4>);
+    case 6: return reinterpret_cast<const void *>(&batch_work_kernel<6>);
+    case 8: return reinterpret_cast<const void *>(&batch_work_kernel<8>);
+    case 12: return reinterpret_cast<const void *>(&batch_work_kernel<12>);
+    case 16: return reinterpret_cast<const void *>(&batch_work_kernel<16>);
+    case 24: return reinterpret_cast<const void *>(&batch_work_kernel<24>);
+    case 32: return reinterpret_cast<const void *>(&batch_work_kernel<32>);
+    default: return nullptr;
+  }
+}
+
 template <int VPT, int W>
 const void *rows_fn_policy(int policy) {
   return policy == kPolicyStreaming
@@ -492,6 +566,7 @@ const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, 
 }
 const void *checksum_kernel_fn(uint32_t vpt, bool banded) { return select_checksum(vpt, banded); }
 const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }
+const void *batch_work_kernel_fn(uint32_t vpt) { return select_batch_work(vpt); }
 const void *init_kernel_fn() { return reinterpret_cast<const void *>(&init_kernel); }
 const void *jump_kernel_fn() { return reinterpret_cast<const void *>(&jump_kernel); }
 

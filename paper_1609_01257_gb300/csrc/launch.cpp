@@ -247,6 +247,21 @@ int batch_blocks_per_sm(uint32_t vpt, uint32_t block) {
   return fn ? occupancy(fn, block) : 0;
 }
 
+int batch_work_blocks_per_sm(uint32_t vpt) {
+  const void *fn = batch_work_kernel_fn(vpt);
+  return fn ? occupancy(fn, kGenBlock) : 0;
+}
+
+cudaError_t launch_batch_work(const BatchWork *work, uint32_t n, uint32_t *counter, uint32_t vpt, uint32_t grid,
+                              cudaStream_t st) {
+  const void *fn = batch_work_kernel_fn(vpt);
+  if (!fn) return cudaErrorInvalidValue;
+  void *params[] = {&work, &n, &counter};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kGenBlock), params, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
 cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint32_t n_units,
                          uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
                          cudaStream_t st) {
