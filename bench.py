@@ -244,6 +244,9 @@ def run_gpu(args, wl):
     vpt, block, grid = gen.launch_config()
     del out
     torch.cuda.empty_cache()
+    # Denominators measured on this GPU, outside the timed regions.
+    write_ceiling = measure_write_ceiling(torch)
+    link = measure_host_link(torch) if not args.skip_e2e else None
 
     # ---- end-to-end leg: host output through the C ABI ------------------------
     e2e = None
@@ -299,7 +302,55 @@ def run_gpu(args, wl):
             "profiled_step": {"read_buffer_s": prof["aggregate"].get("READ_BUFFER", (0, 0))[0],
                               "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0],
                               "overlap_s": sum(prof["overlaps"].values())}}
+        e2e["host_link_GBps"] = link
+        e2e["frac_link"] = e2e["value"] / link
         del host
+
+        # Host consumer (Section 5, "out" block): consumer threads fold every
+        # row into its XOR and sum as it arrives through the staging slots.
+        gh = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+                           profiling=False, init=False)
+
+        def step_host_checksum():
+            gh.init()
+            gh.generate_host_checksum(T)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            step_host_checksum()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_host_checksum()
+        barrier()
+        hc_s = max_over_ranks(time.perf_counter() - t0)
+        gh.close()
+        e2e["host_checksum"] = {"value": nbytes * ws * args.e2e_steps / hc_s / 1e9, "unit": "GB/s",
+                                "ms_per_step": 1e3 * hc_s / args.e2e_steps,
+                                "consumers": "default (half the host cores, 1-8)",
+                                "host_cores": os.cpu_count()}
+
+        # The paper's program as measured there: every value to stdout, here
+        # /dev/null, through the staging slots and one writer thread.
+        gf = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+                           profiling=False, init=False)
+        fd = os.open(os.devnull, os.O_WRONLY)
+
+        def step_fd():
+            gf.init()
+            gf.generate_fd(T, fd)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            step_fd()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_fd()
+        barrier()
+        fd_s = max_over_ranks(time.perf_counter() - t0)
+        os.close(fd)
+        gf.close()
+        e2e["stdout_devnull"] = {"value": nbytes * ws * args.e2e_steps / fd_s / 1e9, "unit": "GB/s",
+                                 "ms_per_step": 1e3 * fd_s / args.e2e_steps}
 
     gen.close()
     if rank != 0:
@@ -321,7 +372,9 @@ def run_gpu(args, wl):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": f"{src}: hbm_gbs (copy, read+write) from MEASURED_PEAKS.json",
-                     "kernel": "rows_kernel", "kernel_avg_ms": k_avg * 1e3, "launches": k_count},
+                     "kernel": "rows_kernel", "kernel_avg_ms": k_avg * 1e3, "launches": k_count,
+                     "write_ceiling_GBps": write_ceiling, "frac_write_ceiling": achieved / write_ceiling,
+                     "write_ceiling_source": "measured here: torch fill_ over 2 GiB, best of 10"},
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,
@@ -336,6 +389,43 @@ def run_gpu(args, wl):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_write_ceiling(torch, nbytes=2 * GIB, reps=10):
+    """Write-only HBM ceiling on this GPU: best of `reps` `fill_` launches over
+    `nbytes` (a plain store stream, no reads), timed with CUDA events."""
+    buf = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    best = float("inf")
+    for r in range(reps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        buf.fill_(float(r))
+        e1.record(s)
+        e1.synchronize()
+        if r >= 2:
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del buf
+    return nbytes / best / 1e9
+
+
+def measure_host_link(torch, nbytes=GIB, reps=10):
+    """Device-to-host link rate: best of `reps` copy-engine copies of `nbytes`
+    into page-locked memory (cudaMemcpyAsync), timed with CUDA events."""
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.current_stream()
+    best = float("inf")
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        host.copy_(dev, non_blocking=True)
+        e1.record(s)
+        e1.synchronize()
+        if r >= 1:
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del dev, host
+    return nbytes / best / 1e9
 
 
 def _json_line(d):
@@ -467,6 +557,52 @@ def run_checksum(args, wl):
     return 0
 
 
+def run_consumer(args, wl):
+    """Host consumer threads of the streamed path: per-row XOR/sum folding
+    (rng_generate_host_checksum) and copies into pageable memory through the
+    staging slots, against the number of consumer threads, on the streaming
+    workload's shape (2^22 streams, 32 MiB rows); one JSON line."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
+    link = measure_host_link(torch)
+    fold, copy = {}, {}
+    for k in args.consumers:
+        g = rng.Generator(n, seed, device_buffer_bytes=wl["device_buffer_bytes"], profiling=False,
+                          host_consumers=k)
+        g.generate_host_checksum(T)
+        best = float("inf")
+        for _ in range(args.steps):
+            g.init()
+            t0 = time.perf_counter()
+            g.generate_host_checksum(T)
+            best = min(best, time.perf_counter() - t0)
+        g.close()
+        fold[k] = 8 * n * T / best / 1e9
+    rows = min(T, 128)  # 4 GiB of pageable memory, touched before timing
+    out = np.ones((rows, n), dtype=np.uint64)
+    for k in args.consumers:
+        g = rng.Generator(n, seed, device_buffer_bytes=wl["device_buffer_bytes"], profiling=False,
+                          host_path=1, host_consumers=k)
+        g.generate_to_host(rows, out)
+        best = float("inf")
+        for _ in range(args.steps):
+            g.init()
+            t0 = time.perf_counter()
+            g.generate_to_host(rows, out)
+            best = min(best, time.perf_counter() - t0)
+        g.close()
+        copy[k] = 8 * n * rows / best / 1e9
+    _json_line({"workload": f"host consumers: {n} streams, 32 MiB rows; fold {T} rows, "
+                            f"pageable copy {rows} rows; best of {args.steps}",
+                "unit": "GB/s", "host_link_GBps": link, "host_cores": os.cpu_count(),
+                "fold_xor_sum": fold, "pageable_copy": copy})
+    return 0
+
+
 def run_queue_chart(args):
     """The run the paper charts (Section 4.2, queue utilisation figure): 2^24
     values per iteration, 8 iterations, the double buffer with one 128 MiB row
@@ -557,7 +693,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart"], default="streaming")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart", "consumer"],
+                    default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
     ap.add_argument("--batch-cap-gib", type=float, default=8.0, help="batched: total output cap")
     ap.add_argument("--batch-vpt", type=int, default=0, help="batched: values per thread (0 = autotune)")
@@ -567,6 +704,8 @@ def main(argv=None):
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
     ap.add_argument("--server-mode", type=int, default=2, help="served: 1 one unit per block, 2 persistent")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
+    ap.add_argument("--consumers", type=int, nargs="+", default=[1, 2, 4, 8, 16],
+                    help="consumer: host consumer thread counts")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
@@ -585,12 +724,14 @@ def main(argv=None):
         return run_sweep(args)
     if args.workload == "queue-chart":
         return run_queue_chart(args)
-    wl = dict(WORKLOADS["streaming" if args.workload == "checksum" else args.workload])
+    wl = dict(WORKLOADS["streaming" if args.workload in ("checksum", "consumer") else args.workload])
     if args.iterations:
         wl["iterations"] = args.iterations
         wl["name"] = re.sub(r"x \d+ iterations", f"x {args.iterations} iterations", wl["name"])
     if args.workload == "checksum":
         return run_checksum(args, wl)
+    if args.workload == "consumer":
+        return run_consumer(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

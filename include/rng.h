@@ -84,8 +84,10 @@ typedef struct rng_opts {
                                      a larger generator); ids g0 .. g0+n-1 */
     uint64_t device_buffer_bytes; /* host output: size of each of the two device
                                      buffers (ping-pong, Section 5); default 32 MiB */
-    uint32_t host_slots;          /* pinned staging slots for pageable host output
-                                     and for sinks; default 2 */
+    uint32_t host_slots;          /* pinned staging slots (device_buffer_bytes
+                                     each) for pageable host output, sinks and
+                                     host checksums; 0 (default) = the host
+                                     consumers + 2, else at least 2 */
     uint32_t profiling;           /* 1 (default): time every kernel and copy with
                                      CUDA events for the profiler */
     void *compute_stream;         /* cudaStream_t for kernels; NULL = own stream */
@@ -109,6 +111,13 @@ typedef struct rng_opts {
                                      1 = always the double buffer of Section 5;
                                      2 = always direct (RNG_EINVAL if the GPU
                                      cannot store into the destination) */
+    uint32_t host_consumers;      /* host threads draining the staging slots
+                                     (at most 64).  0 (default): one for sinks
+                                     (in order), half the host's cores (1-8)
+                                     for pageable copies and host checksums.
+                                     Above 1, a sink is called concurrently
+                                     from several threads, chunks in any
+                                     order; rng_generate_fd always uses one */
 } rng_opts;
 
 void rng_opts_default(rng_opts *opts);
@@ -172,8 +181,10 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev,
 int rng_generate_ring(rng_gen *g, uint64_t iterations, uint64_t *ring_dev,
                       uint64_t ring_rows, rng_err **err);
 
-/* Host consumer ("out" block of Section 5).  Called on a library thread,
- * in order, once per chunk of finished values: `values` holds `rows`
+/* Host consumer ("out" block of Section 5).  Called on a library thread
+ * once per chunk of finished values, in order unless rng_opts.host_consumers
+ * is above 1 (then concurrently from that many threads, in any order):
+ * `values` holds `rows`
  * consecutive iterations starting at absolute iteration `first_iteration`,
  * each row covering streams first_stream .. first_stream+n_streams-1
  * (relative to this generator), rows `row_pitch` values apart.  The
@@ -197,6 +208,20 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink,
  * filled (the host-side dual buffer the paper names as an improvement).
  * Blocks until everything is written; RNG_ESINK if a write fails. */
 int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err);
+
+/* Host-side check of streamed output (the consumer of the paper's streaming
+ * program, Section 5, "out" block): streams iterations p .. p+iterations-1
+ * over the host link through the double buffer and the pinned staging slots,
+ * and the host consumer threads (rng_opts.host_consumers) fold every row
+ * into its XOR (row_xor_host[it-p]) and wrapping sum modulo 2^64
+ * (row_sum_host[it-p]) over all streams, releasing each slot as soon as it
+ * is folded; the values themselves are not kept.  Both arrays are
+ * caller-owned host memory of `iterations` uint64 words; the call clears
+ * them first and blocks until every row is folded.  Same values as
+ * rng_generate_checksum, computed on the host after the link instead of on
+ * the device.  Errors as rng_generate with host output. */
+int rng_generate_host_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_host,
+                               uint64_t *row_sum_host, rng_err **err);
 
 /* Generate-and-checksum mode: advances the streams through iterations
  * p .. p+iterations-1 without storing the values and writes, for each

@@ -45,6 +45,7 @@ class RngOpts(ctypes.Structure):
         ("store_width", c_u32),
         ("grid_blocks", c_u32),
         ("host_path", c_u32),
+        ("host_consumers", c_u32),
     ]
 
 
@@ -98,6 +99,7 @@ SIGNATURES = {
     "rng_generate_sink": ([c_vp, c_u64, SINK_FN, c_vp, P_err], c_int),
     "rng_generate_ring": ([c_vp, c_u64, c_vp, c_u64, P_err], c_int),
     "rng_generate_fd": ([c_vp, c_u64, c_int, P_err], c_int),
+    "rng_generate_host_checksum": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
     "rng_generate_checksum": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
     "rng_skip": ([c_vp, c_u64, P_err], c_int),
     "rng_position": ([c_vp, P_u64], c_int),

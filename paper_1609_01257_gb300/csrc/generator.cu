@@ -200,7 +200,9 @@ int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh
   return rc;
 }
 
-int ensure_buffers(rng_gen *g, bool staged, rng_err **err) {
+// Device buffers and events of the double buffer; with `slots` > 0, at least
+// that many pinned staging slots (grown on demand, kept until rng_destroy).
+int ensure_buffers(rng_gen *g, size_t slots, rng_err **err) {
   if (!g->d_buf[0]) {
     for (int b = 0; b < 2; ++b) {
       int rc = rngi::cuda_fail(err, cudaMalloc(&g->d_buf[b], g->buf_bytes), "cudaMalloc(device buffer)");
@@ -213,19 +215,19 @@ int ensure_buffers(rng_gen *g, bool staged, rng_err **err) {
       if (rc) return rc;
     }
   }
-  if (staged && g->h_slots.empty()) {
-    const uint32_t n = g->opts.host_slots < 2 ? 2 : g->opts.host_slots;
-    for (uint32_t i = 0; i < n; ++i) {
-      void *p = nullptr;
-      int rc = rngi::cuda_fail(err, cudaHostAlloc(&p, g->buf_bytes, cudaHostAllocDefault),
-                               "cudaHostAlloc(staging slot)");
-      if (rc) return rc;
-      g->h_slots.push_back(p);
-      cudaEvent_t e;
-      rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
-      if (rc) return rc;
-      g->slot_ready.push_back(e);
+  while (g->h_slots.size() < slots) {
+    void *p = nullptr;
+    int rc = rngi::cuda_fail(err, cudaHostAlloc(&p, g->buf_bytes, cudaHostAllocDefault),
+                             "cudaHostAlloc(staging slot)");
+    if (rc) return rc;
+    cudaEvent_t e;
+    rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc) {
+      cudaFreeHost(p);
+      return rc;
     }
+    g->h_slots.push_back(p);
+    g->slot_ready.push_back(e);
   }
   return RNG_OK;
 }
@@ -274,7 +276,44 @@ int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_
   return gen_launch_rows(g, a, sh, err);
 }
 
-// Host consumer thread for staged output (pageable destination or sink).
+// What the host consumers do with each finished staging slot.
+struct Target {
+  uint64_t *out_host = nullptr;  // pageable destination: copy the chunk there
+  rng_sink_fn sink = nullptr;    // or hand it to a sink
+  void *user = nullptr;
+  uint64_t *row_xor = nullptr;   // or fold it into per-row XOR / sum
+  uint64_t *row_sum = nullptr;
+  unsigned consumers = 1;        // host threads draining the slots
+};
+
+// XOR and wrapping sum of `n` values; four independent lanes so that the
+// loop is bound by the memory reads, not by one dependency chain.
+void xor_sum(const uint64_t *v, uint64_t n, uint64_t *x_out, uint64_t *s_out) {
+  uint64_t x0 = 0, x1 = 0, x2 = 0, x3 = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  uint64_t k = 0;
+  for (; k + 4 <= n; k += 4) {
+    x0 ^= v[k];
+    x1 ^= v[k + 1];
+    x2 ^= v[k + 2];
+    x3 ^= v[k + 3];
+    s0 += v[k];
+    s1 += v[k + 1];
+    s2 += v[k + 2];
+    s3 += v[k + 3];
+  }
+  for (; k < n; ++k) {
+    x0 ^= v[k];
+    s0 += v[k];
+  }
+  *x_out = x0 ^ x1 ^ x2 ^ x3;
+  *s_out = s0 + s1 + s2 + s3;
+}
+
+// Host consumer threads for staged output (the "out" block of Section 5, with
+// the host-side buffering the paper names as an improvement): each takes the
+// next finished slot, waits for its copy, copies it to a pageable
+// destination, hands it to a sink, or folds it into per-row checksums, and
+// frees the slot.  With one thread, chunks are consumed in order.
 struct Consumer {
   struct Job {
     Chunk c;
@@ -282,17 +321,42 @@ struct Consumer {
     bool stop;
   };
   rng_gen *g;
-  uint64_t *out_host;
+  Target t;
   uint64_t first_iteration;
-  rng_sink_fn sink;
-  void *user;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Job> jobs;
   std::vector<bool> slot_free;
   int status = RNG_OK;
   std::string msg;
-  std::thread th;
+  std::vector<std::thread> th;
+
+  int consume(const Job &j, std::string *m) {
+    cudaError_t st = cudaEventSynchronize(g->slot_ready[j.slot]);
+    if (st != cudaSuccess) {
+      *m = std::string("cudaEventSynchronize: ") + cudaGetErrorString(st);
+      return RNG_ECUDA;
+    }
+    const uint64_t *vals = static_cast<const uint64_t *>(g->h_slots[j.slot]);
+    if (t.out_host) {
+      memcpy(t.out_host + j.c.r0 * g->n + j.c.s0, vals, j.c.rows * j.c.span * 8);
+    } else if (t.sink) {
+      int urc = t.sink(t.user, first_iteration + j.c.r0, j.c.rows, j.c.s0, j.c.span, j.c.span, vals);
+      if (urc) {
+        *m = "host consumer returned " + std::to_string(urc);
+        return RNG_ESINK;
+      }
+    } else {
+      // Column slabs of one row may be folded by different threads.
+      for (uint64_t r = 0; r < j.c.rows; ++r) {
+        uint64_t x, s;
+        xor_sum(vals + r * j.c.span, j.c.span, &x, &s);
+        __atomic_fetch_xor(&t.row_xor[j.c.r0 + r], x, __ATOMIC_RELAXED);
+        __atomic_fetch_add(&t.row_sum[j.c.r0 + r], s, __ATOMIC_RELAXED);
+      }
+    }
+    return RNG_OK;
+  }
 
   void run() {
     for (;;) {
@@ -304,31 +368,13 @@ struct Consumer {
         jobs.pop_front();
       }
       if (j.stop) return;
-      int rc = RNG_OK;
-      std::string m;
+      bool skip;
       {
-        bool skip;
-        {
-          std::lock_guard<std::mutex> lk(mu);
-          skip = status != RNG_OK;
-        }
-        if (!skip) {
-          cudaError_t st = cudaEventSynchronize(g->slot_ready[j.slot]);
-          const uint64_t *vals = static_cast<const uint64_t *>(g->h_slots[j.slot]);
-          if (st != cudaSuccess) {
-            rc = RNG_ECUDA;
-            m = std::string("cudaEventSynchronize: ") + cudaGetErrorString(st);
-          } else if (out_host) {
-            memcpy(out_host + j.c.r0 * g->n + j.c.s0, vals, j.c.rows * j.c.span * 8);
-          } else {
-            int urc = sink(user, first_iteration + j.c.r0, j.c.rows, j.c.s0, j.c.span, j.c.span, vals);
-            if (urc) {
-              rc = RNG_ESINK;
-              m = "host consumer returned " + std::to_string(urc);
-            }
-          }
-        }
+        std::lock_guard<std::mutex> lk(mu);
+        skip = status != RNG_OK;
       }
+      std::string m;
+      const int rc = skip ? RNG_OK : consume(j, &m);
       {
         std::lock_guard<std::mutex> lk(mu);
         if (rc != RNG_OK && status == RNG_OK) {
@@ -342,19 +388,31 @@ struct Consumer {
   }
 };
 
-int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn sink, void *user,
-                     rng_err **err) {
+// Host consumer threads used when the caller does not choose: half the
+// host's cores, 1 to 8.
+unsigned auto_consumers() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return std::max(1u, std::min(8u, hw / 2));
+}
+
+int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
   bool pinned = false;
-  if (out_host) {
+  if (tgt.out_host) {
     cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost)
+    if (cudaPointerGetAttributes(&attr, tgt.out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost)
       pinned = true;
     cudaGetLastError();
   }
   const bool staged = !pinned;
-  int rc = ensure_buffers(g, staged, err);
-  if (rc) return rc;
   const std::vector<Chunk> chunks = plan_chunks(g->n, T, g->buf_bytes);
+  // No more consumers than chunks; two slots beyond the consumers keep the
+  // copy engine busy while every consumer holds one.
+  tgt.consumers = static_cast<unsigned>(std::max<size_t>(1, std::min<size_t>(tgt.consumers, chunks.size())));
+  size_t slots = 0;
+  if (staged) slots = g->opts.host_slots ? std::max<uint32_t>(2, g->opts.host_slots) : tgt.consumers + 2;
+  int rc = ensure_buffers(g, slots, err);
+  if (rc) return rc;
+  if (staged) slots = g->h_slots.size();
   reserve_events(g, 2 * chunks.size());  // one kernel and one read per chunk
   const bool hash_first_rows = !g->materialized;
   const uint64_t first_it = g->pos;
@@ -362,13 +420,21 @@ int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn s
 
   Consumer cons;
   cons.g = g;
-  cons.out_host = out_host;
+  cons.t = tgt;
   cons.first_iteration = first_it;
-  cons.sink = sink;
-  cons.user = user;
   if (staged) {
-    cons.slot_free.assign(g->h_slots.size(), true);
-    cons.th = std::thread([&cons] { cons.run(); });
+    cons.slot_free.assign(slots, true);
+    for (unsigned k = 0; k < tgt.consumers; ++k) {
+      try {
+        cons.th.emplace_back([&cons] { cons.run(); });
+      } catch (...) {
+        break;  // run with the threads that could be started
+      }
+    }
+    if (cons.th.empty()) {
+      g->initialized = true;  // nothing was launched
+      return rngi::fail(err, RNG_ENOMEM, "rng_generate: cannot start a host consumer thread");
+    }
   }
   const auto wait_limit = std::chrono::milliseconds(g->opts.host_wait_ms ? g->opts.host_wait_ms : 600000);
 
@@ -379,10 +445,11 @@ int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn s
     const int b = static_cast<int>(c & 1);
     size_t slot = 0;
     if (staged) {
-      slot = c % g->h_slots.size();
       std::unique_lock<std::mutex> lk(cons.mu);
-      const bool ok = cons.cv.wait_for(lk, wait_limit,
-                                       [&] { return cons.slot_free[slot] || cons.status != RNG_OK; });
+      const bool ok = cons.cv.wait_for(lk, wait_limit, [&] {
+        return cons.status != RNG_OK ||
+               std::find(cons.slot_free.begin(), cons.slot_free.end(), true) != cons.slot_free.end();
+      });
       if (cons.status != RNG_OK) break;
       if (!ok) {
         status = RNG_ETIMEOUT;
@@ -390,6 +457,8 @@ int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn s
         cons.status = RNG_ETIMEOUT;
         break;
       }
+      slot = static_cast<size_t>(std::find(cons.slot_free.begin(), cons.slot_free.end(), true) -
+                                 cons.slot_free.begin());
       cons.slot_free[slot] = false;
     }
     cudaError_t st = cudaSuccess;
@@ -400,7 +469,7 @@ int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn s
     st = cudaEventRecord(g->produced[b], g->compute);
     if (st == cudaSuccess) st = cudaStreamWaitEvent(g->copy, g->produced[b], 0);
     if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "event ordering"); break; }
-    void *dst = staged ? g->h_slots[slot] : static_cast<void *>(out_host + ck.r0 * g->n + ck.s0);
+    void *dst = staged ? g->h_slots[slot] : static_cast<void *>(tgt.out_host + ck.r0 * g->n + ck.s0);
     long op = op_begin(g, "READ_BUFFER", kQueueComms, g->copy);
     st = cudaMemcpyAsync(dst, g->d_buf[b], ck.rows * ck.span * 8, cudaMemcpyDeviceToHost, g->copy);
     op_end(g, op, g->copy);
@@ -418,10 +487,10 @@ int double_buffer_host(rng_gen *g, uint64_t T, uint64_t *out_host, rng_sink_fn s
   if (staged) {
     {
       std::lock_guard<std::mutex> lk(cons.mu);
-      cons.jobs.push_back({Chunk{}, 0, true});
+      for (size_t k = 0; k < cons.th.size(); ++k) cons.jobs.push_back({Chunk{}, 0, true});
     }
     cons.cv.notify_all();
-    cons.th.join();
+    for (std::thread &th : cons.th) th.join();
     if (status == RNG_OK && cons.status != RNG_OK) {
       status = cons.status;
       status_msg = cons.msg;
@@ -513,7 +582,7 @@ void rng_opts_default(rng_opts *o) {
   o->fuse_init = 1;
   o->stream_offset = 0;
   o->device_buffer_bytes = size_t(32) << 20;
-  o->host_slots = 2;
+  o->host_slots = 0;
   o->profiling = 1;
   o->compute_stream = nullptr;
   o->device = -1;
@@ -547,6 +616,7 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
     return rngi::fail(err, RNG_EINVAL, "rng_create: device_buffer_bytes must be a positive multiple of 16");
   if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
   if (o.host_path > 2) return rngi::fail(err, RNG_EINVAL, "rng_create: host_path must be 0, 1 or 2");
+  if (o.host_consumers > 64) return rngi::fail(err, RNG_EINVAL, "rng_create: host_consumers must be at most 64");
   if (o.store_width != 0 && o.store_width != 1 && o.store_width != 2 && o.store_width != 4)
     return rngi::fail(err, RNG_EINVAL, "rng_create: store_width must be 0, 1, 2 or 4");
   if (o.stream_offset > (uint64_t(1) << 32) - streams)
@@ -648,7 +718,10 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
     if (g->opts.host_path == 2 && !can)
       return rngi::fail(err, RNG_EINVAL, "rng_generate: the GPU cannot store into this host memory (host_path = 2)");
     if (can) return direct_host(g, iterations, dptr, err);
-    return double_buffer_host(g, iterations, out_host, nullptr, nullptr, err);
+    Target tgt;
+    tgt.out_host = out_host;
+    tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : auto_consumers();
+    return double_buffer_host(g, iterations, tgt, err);
   }
   if (reinterpret_cast<uintptr_t>(out_dev) % 8)
     return rngi::fail(err, RNG_EINVAL, "rng_generate: out_dev must be 8-byte aligned");
@@ -707,7 +780,11 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink, void *u
   if (iterations == 0) return RNG_OK;
   rc = size_ok(g->n, iterations, err);
   if (rc) return rc;
-  return double_buffer_host(g, iterations, nullptr, sink, user, err);
+  Target tgt;
+  tgt.sink = sink;
+  tgt.user = user;
+  tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : 1;
+  return double_buffer_host(g, iterations, tgt, err);
 }
 
 // Sink of rng_generate_fd: writes each chunk's bytes to the descriptor,
@@ -730,9 +807,39 @@ static int fd_sink(void *user, uint64_t, uint64_t rows, uint64_t, uint64_t n_str
 }
 
 int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err) {
+  int rc = check_gen(g, err, "rng_generate_fd");
+  if (rc) return rc;
   if (fd < 0) return rngi::fail(err, RNG_EINVAL, "rng_generate_fd: bad file descriptor %d", fd);
+  if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_generate_fd: generator not initialised (call rng_init)");
+  if (iterations == 0) return RNG_OK;
+  rc = size_ok(g->n, iterations, err);
+  if (rc) return rc;
   int user = fd;
-  return rng_generate_sink(g, iterations, fd_sink, &user, err);
+  Target tgt;
+  tgt.sink = fd_sink;
+  tgt.user = &user;
+  tgt.consumers = 1;  // the bytes must reach the descriptor in order
+  return double_buffer_host(g, iterations, tgt, err);
+}
+
+int rng_generate_host_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_host, uint64_t *row_sum_host,
+                               rng_err **err) {
+  int rc = check_gen(g, err, "rng_generate_host_checksum");
+  if (rc) return rc;
+  if (!row_xor_host || !row_sum_host)
+    return rngi::fail(err, RNG_EINVAL, "rng_generate_host_checksum: NULL output");
+  if (!g->initialized)
+    return rngi::fail(err, RNG_ESTATE, "rng_generate_host_checksum: generator not initialised (call rng_init)");
+  if (iterations == 0) return RNG_OK;
+  rc = size_ok(g->n, iterations, err);
+  if (rc) return rc;
+  memset(row_xor_host, 0, iterations * 8);
+  memset(row_sum_host, 0, iterations * 8);
+  Target tgt;
+  tgt.row_xor = row_xor_host;
+  tgt.row_sum = row_sum_host;
+  tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : auto_consumers();
+  return double_buffer_host(g, iterations, tgt, err);
 }
 
 int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev, uint64_t *row_sum_dev,

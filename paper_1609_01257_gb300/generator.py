@@ -33,7 +33,7 @@ class Generator:
 
     def __init__(self, streams: int, seed: int = 0, *, values_per_thread: int = 0,
                  fuse_init: bool = True, stream_offset: int = 0,
-                 device_buffer_bytes: int = 32 << 20, host_slots: int = 2,
+                 device_buffer_bytes: int = 32 << 20, host_slots: int = 0, host_consumers: int = 0,
                  profiling: bool = True, compute_stream=None, device: Optional[int] = None,
                  store_policy: int = 1, host_wait_ms: int = 0, store_width: int = 0,
                  block_threads: int = 0, grid_blocks: int = 0, host_path: int = 0, init: bool = True):
@@ -45,6 +45,7 @@ class Generator:
         o.stream_offset = stream_offset
         o.device_buffer_bytes = device_buffer_bytes
         o.host_slots = host_slots
+        o.host_consumers = host_consumers
         o.profiling = 1 if profiling else 0
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         if compute_stream is None:
@@ -168,7 +169,9 @@ class Generator:
         """Streams ``iterations`` rows through the pinned staging slots and
         calls ``sink(first_iteration, block, first_stream)`` per chunk, where
         ``block`` is a ``(rows, n_streams)`` uint64 view valid only during the
-        call.  A truthy return value stops the run."""
+        call.  A truthy return value stops the run.  In order, unless the
+        generator was made with ``host_consumers`` above 1 (then from that
+        many threads, in any order)."""
         failure = []
 
         def _cb(_user, first_it, rows, first_stream, n_streams, pitch, values):
@@ -188,6 +191,17 @@ class Generator:
             if failure:
                 raise failure[0]
             raise
+
+    def generate_host_checksum(self, iterations: int):
+        """Streams ``iterations`` rows over the host link and folds each row
+        on the host into its XOR and wrapping sum (two uint64 numpy arrays);
+        the values are not kept."""
+        row_xor = np.empty(iterations, dtype=np.uint64)
+        row_sum = np.empty(iterations, dtype=np.uint64)
+        if iterations:
+            C.check(self._lib.rng_generate_host_checksum, self._h, iterations,
+                    ctypes.c_void_p(row_xor.ctypes.data), ctypes.c_void_p(row_sum.ctypes.data))
+        return row_xor, row_sum
 
     def generate_fd(self, iterations: int, fd: int):
         """Stream ``iterations`` rows as raw uint64 values to file descriptor ``fd``."""

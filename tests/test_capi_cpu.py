@@ -69,6 +69,20 @@ def test_bad_arguments_return_status_not_crash(L):
     assert L.rng_batch_create(0, None, None, None, None, None, ctypes.byref(h), None) == C.RNG_EINVAL
 
 
+def test_option_structs_match_the_header(L):
+    # Each *_opts_default writes sizeof() of the C struct into struct_size; the
+    # binding's ctypes layout must have the same size and defaults.
+    for cls, fn in [(C.RngOpts, L.rng_opts_default), (C.RngBatchOpts, L.rng_batch_opts_default),
+                    (C.RngServerOpts, L.rng_server_opts_default)]:
+        o = cls()
+        fn(ctypes.byref(o))
+        assert o.struct_size == ctypes.sizeof(cls), cls.__name__
+    o = C.RngOpts()
+    L.rng_opts_default(ctypes.byref(o))
+    assert (o.host_slots, o.host_consumers, o.host_path, o.store_policy, o.fuse_init) == (0, 0, 0, 1, 1)
+    assert o.device_buffer_bytes == 32 << 20 and o.profiling == 1 and o.device == -1
+
+
 def test_create_without_gpu_fails_cleanly(L):
     import torch
     if torch.cuda.is_available():

@@ -1,0 +1,116 @@
+"""Host consumer threads of the streamed path (Section 5, "out" block):
+per-row XOR / wrapping-sum folding on the host, several threads draining the
+staging slots, and pageable copies split across them.  Every result is
+compared with the oracle."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1609_01257_gb300 as rng
+
+pytestmark = pytest.mark.gpu
+
+
+# (streams, iterations, device buffer bytes): whole rows per chunk, a ragged
+# last chunk, and rows split into column slabs (buffer smaller than a row,
+# odd widths) so that several threads fold parts of one row.
+CASES = [
+    (1, 9, 64),
+    (1000, 37, 8 * 1000 * 5),
+    (4097, 20, 8 * 4097 * 3 + 8),  # device buffers are multiples of 16 bytes
+    (30_001, 7, 8 * 4096),
+    (262_147, 5, 8 * 65_536),
+]
+
+
+@pytest.mark.parametrize("n,T,buf", CASES)
+@pytest.mark.parametrize("consumers", [1, 3, 8])
+def test_host_checksum_matches_oracle(n, T, buf, consumers):
+    g = rng.Generator(n, 21, device_buffer_bytes=buf, host_consumers=consumers)
+    rx, rs = g.generate_host_checksum(T)
+    tail = g.generate(2).cpu().numpy()  # the streams advanced by T
+    g.close()
+    wx, ws, _ = oracle.row_checksums(n, 21, T)
+    assert np.array_equal(rx, wx) and np.array_equal(rs, ws)
+    assert np.array_equal(tail, oracle.generate(n, 21, 2, p0=T))
+
+
+def test_host_checksum_equals_device_checksum_after_position():
+    # Started mid-stream: both checksum forms cover the same iterations.
+    n = 50_000
+    g = rng.Generator(n, 3, device_buffer_bytes=8 * n * 2)
+    g.generate(11)
+    hx, hs = g.generate_host_checksum(13)
+    g.close()
+    g = rng.Generator(n, 3)
+    g.generate(11)
+    dx, ds = g.generate_checksum(13)
+    g.sync()
+    dx, ds = dx.cpu().numpy(), ds.cpu().numpy()
+    g.close()
+    assert np.array_equal(hx, dx) and np.array_equal(hs, ds)
+    wx, ws, _ = oracle.row_checksums(n, 3, 13, p0=11)
+    assert np.array_equal(hx, wx) and np.array_equal(hs, ws)
+
+
+def test_host_checksum_zero_iterations_and_not_initialised():
+    g = rng.Generator(100, 1, init=False)
+    with pytest.raises(rng.RngError) as e:
+        g.generate_host_checksum(3)
+    assert e.value.code == 4
+    g.init()
+    rx, rs = g.generate_host_checksum(0)
+    assert rx.size == 0 and rs.size == 0
+    assert np.array_equal(g.generate(1).cpu().numpy(), oracle.generate(100, 1, 1))
+    g.close()
+
+
+def test_concurrent_sink_sees_every_chunk_once():
+    n, T = 3000, 40
+    g = rng.Generator(n, 6, device_buffer_bytes=8 * n * 3, host_consumers=4)
+    got = np.zeros((T, n), dtype=np.uint64)
+    seen = []
+    lock = threading.Lock()
+
+    def sink(first_it, block, first_stream):
+        with lock:
+            seen.append(first_it)
+        got[first_it:first_it + block.shape[0], first_stream:first_stream + block.shape[1]] = block
+
+    g.generate_sink(T, sink)
+    g.close()
+    assert sorted(seen) == list(range(0, T, 3))
+    assert np.array_equal(got, oracle.generate(n, 6, T))
+
+
+@pytest.mark.parametrize("consumers", [1, 4])
+def test_pageable_copy_with_consumers(consumers):
+    # Double buffer into pageable memory: copies out of the staging slots
+    # are spread over the consumer threads.
+    n, T = 70_001, 9
+    g = rng.Generator(n, 8, device_buffer_bytes=8 * 20_000, host_path=1, host_consumers=consumers)
+    out = np.zeros((T, n), dtype=np.uint64)
+    g.generate_to_host(T, out)
+    g.close()
+    assert np.array_equal(out, oracle.generate(n, 8, T))
+
+
+def test_fd_output_in_order_with_consumers(tmp_path):
+    # rng_generate_fd keeps one consumer whatever host_consumers says: the
+    # bytes reach the file in stream order.
+    n, T = 5000, 12
+    g = rng.Generator(n, 4, device_buffer_bytes=8 * n, host_consumers=6)
+    path = tmp_path / "out.bin"
+    with open(path, "wb") as f:
+        g.generate_fd(T, f.fileno())
+    g.close()
+    got = np.fromfile(path, dtype=np.uint64).reshape(T, n)
+    assert np.array_equal(got, oracle.generate(n, 4, T))
+
+
+def test_host_consumers_bound():
+    with pytest.raises(rng.RngError) as e:
+        rng.Generator(16, 1, host_consumers=65)
+    assert e.value.code == 1

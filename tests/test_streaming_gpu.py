@@ -63,6 +63,19 @@ def test_direct_to_host_full_size_checksums():
         assert np.array_equal(x, wx[i0:i0 + 64]) and np.array_equal(s, ws[i0:i0 + 64]), i0
 
 
+def test_host_checksum_full_size():
+    # The same run folded on the host: the consumer threads reduce each
+    # 32 MiB row as it arrives over the link, in the configuration the
+    # benchmark's host-consumer leg times.
+    cfg = workloads.STREAMING
+    n, T, seed = cfg["streams"], cfg["iterations"], cfg["seed"]
+    g = rng.Generator(n, seed, device_buffer_bytes=cfg["device_buffer_bytes"])
+    rx, rs = g.generate_host_checksum(T)
+    g.close()
+    wx, ws, _ = oracle.row_checksums(n, seed, T)
+    assert np.array_equal(rx, wx) and np.array_equal(rs, ws)
+
+
 def test_checksum_mode_largest_sweep_point():
     # The sweep's largest point: 2^28 streams x 8 iterations in
     # generate-and-checksum mode, in the launch shape the sweep times.  XOR
