@@ -45,6 +45,10 @@ WORKLOADS = {
                   name="plain method: 2^16 streams x 100 iterations, seed 0"),
 }
 
+# ALU-pipe lane operations per value of checksum_kernel<16>, from its ncu
+# capture: 85.6 % ALU-pipe utilisation x 64 lanes x 152 SMs x 1.85 GHz x
+# 184.3 us over 2^22 x 64 values.
+CHECKSUM_ALU_OPS_PER_VALUE = 10.6
 METRIC = "GB/s of uint64 PRNG output (device and host-streamed) vs roofline; p50/p99 req latency"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rows_kernel_traffic.md")
 
@@ -150,6 +154,38 @@ def cpu_oracle_sample(streams: int, seed: int, iterations: int):
     out = oracle.generate(streams, seed, iterations)
     dt = time.perf_counter() - t0
     return out.nbytes, dt
+
+
+def _oracle_worker_init():
+    sys.path.insert(0, ROOT)
+    import oracle  # test infrastructure: the CPU baseline leg only
+    oracle.lib()
+
+
+def _oracle_worker(job):
+    import oracle
+    n_sub, g0, seed, rows = job
+    return oracle.generate(n_sub, seed, rows, g0=g0).nbytes
+
+
+def cpu_oracle_all_cores(streams: int, seed: int, iterations: int):
+    """The same oracle, unchanged, run as one process per host core, each on a
+    contiguous block of stream ids (the values of the whole workload, in
+    column blocks).  Returns (bytes, seconds, processes)."""
+    import multiprocessing as mp
+    sys.path.insert(0, ROOT)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per = (streams + cores - 1) // cores
+    jobs = [(min(per, streams - g0), g0, seed, iterations) for g0 in range(0, streams, per)]
+    # spawn: this process already holds a CUDA context
+    with mp.get_context("spawn").Pool(len(jobs), initializer=_oracle_worker_init) as pool:
+        pool.map(_oracle_worker, [(1, 0, seed, 1)] * len(jobs), chunksize=1)
+        t0 = time.perf_counter()
+        nbytes = sum(pool.map(_oracle_worker, jobs, chunksize=1))
+        dt = time.perf_counter() - t0
+    return nbytes, dt, len(jobs)
 
 
 def run_reference(args, wl):
@@ -385,6 +421,11 @@ def run_gpu(args, wl):
         line["cpu_baseline"] = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} streams x first {rows} iterations ({nb / GIB:.1f} GiB), "
                                           f"single-threaded C oracle, {dt:.1f} s"}
+        nb_all, dt_all, procs = cpu_oracle_all_cores(n, seed, rows)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": nb_all / dt_all / 1e9, "unit": "GB/s", "cores": procs,
+            "sample": f"the same {nb_all / GIB:.1f} GiB as {procs} processes of the oracle on contiguous "
+                      f"stream-id blocks, {dt_all:.1f} s"}
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
@@ -537,6 +578,8 @@ def run_checksum(args, wl):
         step()
     g.sync()
     g.profile_reset()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s = g.stream
     e0.record(s)
@@ -545,15 +588,37 @@ def run_checksum(args, wl):
     e1.record(s)
     e1.synchronize()
     secs = e0.elapsed_time(e1) * 1e-3
+    clk = clocks.stop()
     c, t = g.profile_stat("CHECKSUM_KERNEL")
     g.close()
     props = torch.cuda.get_device_properties(0)
     vps = n * T * args.steps / secs
-    _json_line({"workload": wl["name"] + " (generate-and-checksum mode)", "values_per_s": vps,
-                "equiv_GBps": 8 * vps / 1e9, "kernel_avg_ms": 1e3 * t / max(c, 1), "steps": args.steps,
-                "sms": props.multi_processor_count,
-                "note": "ALU roofline: thread-instructions per value from the ncu summary x values/s, "
-                        "against SMs x 128 lanes x SM clock"})
+    # Integer-ALU roofline: the ALU pipe retires 64 lane-ops per SM per clock
+    # (half a warp instruction per cycle per sub-partition); the ops per
+    # value come from the kernel's ncu capture (ALU-pipe share x pipe peak x
+    # duration / values).
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0  # nominal maximum when nvidia-smi gave no sample
+    peak = props.multi_processor_count * 64 * sm_mhz * 1e6 / 1e12
+    achieved = vps * CHECKSUM_ALU_OPS_PER_VALUE / 1e12
+    line = {"workload": wl["name"] + " (generate-and-checksum mode)", "values_per_s": vps,
+            "equiv_GBps": 8 * vps / 1e9, "kernel_avg_ms": 1e3 * t / max(c, 1), "steps": args.steps,
+            "sms": props.multi_processor_count,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (ALU-pipe lane ops)",
+                         "frac": achieved / peak, "alu_ops_per_value": CHECKSUM_ALU_OPS_PER_VALUE,
+                         "peak_source": "SMs x 64 ALU lanes x median SM clock under load"},
+            "clocks": clk}
+    if not args.skip_cpu_baseline:
+        sys.path.insert(0, ROOT)
+        import oracle  # test infrastructure: the CPU baseline leg only
+        oracle.build()
+        rows = min(T, args.cpu_rows or T)
+        t0 = time.perf_counter()
+        oracle.row_checksums(n, seed, rows)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n * rows / dt, "unit": "values/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n} streams x first {rows} iterations, row checksums, "
+                                          f"single-threaded C oracle, {dt:.1f} s"}
+    _json_line(line)
     return 0
 
 

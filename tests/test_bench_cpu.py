@@ -45,3 +45,10 @@ def test_reference_arm_prints_one_json_line(capsys):
     assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+
+
+def test_all_cores_oracle_baseline_covers_every_stream():
+    # One process per host core on contiguous stream-id blocks: together they
+    # produce exactly the workload's bytes.
+    nbytes, secs, procs = bench.cpu_oracle_all_cores(10_007, 3, 5)
+    assert nbytes == 8 * 10_007 * 5 and secs > 0 and 1 <= procs <= (os.cpu_count() or 1)
