@@ -113,8 +113,8 @@ typedef struct rng_opts {
                                      cannot store into the destination) */
     uint32_t host_consumers;      /* host threads draining the staging slots
                                      (at most 64).  0 (default): one for sinks
-                                     (in order), half the host's cores (1-8)
-                                     for pageable copies and host checksums.
+                                     (in order); for pageable copies and host
+                                     checksums, the host's cores but one (1-16).
                                      Above 1, a sink is called concurrently
                                      from several threads, chunks in any
                                      order; rng_generate_fd always uses one */

@@ -388,11 +388,13 @@ struct Consumer {
   }
 };
 
-// Host consumer threads used when the caller does not choose: half the
-// host's cores, 1 to 8.
+// Host consumer threads used when the caller does not choose: every host
+// core but one (left to the thread issuing launches and copies), 1 to 16.
+// Folding and copying a slot are bound by each core's memory bandwidth
+// (about 18-20 GB/s per Grace core), so the link rate needs most cores.
 unsigned auto_consumers() {
   const unsigned hw = std::thread::hardware_concurrency();
-  return std::max(1u, std::min(8u, hw / 2));
+  return std::max(1u, std::min(16u, hw > 1 ? hw - 1 : 1u));
 }
 
 int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
