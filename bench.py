@@ -626,6 +626,43 @@ def run_checksum(args, wl):
     return 0
 
 
+def run_skip(args):
+    """Jump-ahead (rng_skip): every stream advanced by k = 2^40 + 12345
+    iterations, one GF(2) matrix-vector product per state; 8 bytes read and
+    8 written per stream.  Kernel time from the library's events."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    peaks, src = _peaks()
+    k = (1 << 40) + 12345
+    points = []
+    for n in args.skip_streams:
+        g = rng.Generator(n, 1)
+        g.skip(1)  # materialises the states from the hash
+        for _ in range(args.warmup):
+            g.skip(k)
+        g.sync()
+        g.profile_reset()
+        s = g.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            g.skip(k)
+        e1.record(s)
+        e1.synchronize()
+        c, kt = g.profile_stat("SKIP_KERNEL")
+        g.close()
+        kern = kt / max(c, 1)
+        gbs = 16 * n / kern / 1e9
+        points.append({"streams": n, "call_ms": e0.elapsed_time(e1) / args.steps, "kernel_ms": 1e3 * kern,
+                       "states_per_s": n / kern, "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]})
+    _json_line({"workload": "jump-ahead by 2^40 + 12345 iterations", "unit": "GB/s of state read + written",
+                "peak": peaks["hbm_gbs"], "peak_source": f"{src}: hbm_gbs (copy) from MEASURED_PEAKS.json",
+                "points": points, "steps": args.steps})
+    return 0
+
+
 def run_consumer(args, wl):
     """Host consumer threads of the streamed path: per-row XOR/sum folding
     (rng_generate_host_checksum) and copies into pageable memory through the
@@ -762,7 +799,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart", "consumer"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart", "consumer", "skip"],
                     default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
     ap.add_argument("--batch-cap-gib", type=float, default=8.0, help="batched: total output cap")
@@ -773,6 +810,8 @@ def main(argv=None):
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
     ap.add_argument("--server-mode", type=int, default=2, help="served: 1 one unit per block, 2 persistent")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
+    ap.add_argument("--skip-streams", type=int, nargs="+", default=[1 << 22, 1 << 26, 1 << 28],
+                    help="skip: stream counts")
     ap.add_argument("--consumers", type=int, nargs="+", default=[1, 2, 4, 8, 16],
                     help="consumer: host consumer thread counts")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -793,6 +832,8 @@ def main(argv=None):
         return run_sweep(args)
     if args.workload == "queue-chart":
         return run_queue_chart(args)
+    if args.workload == "skip":
+        return run_skip(args)
     wl = dict(WORKLOADS["streaming" if args.workload in ("checksum", "consumer") else args.workload])
     if args.iterations:
         wl["iterations"] = args.iterations

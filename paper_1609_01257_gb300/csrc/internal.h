@@ -49,7 +49,7 @@ struct RowsLaunch {
   int write_state;      // store the advanced states back
   uint64_t ring_rows;   // 0, or rows wrap around a ring of this many rows
   uint64_t band_rows;   // 0, or rows are split into bands of this many rows
-  const uint64_t *jump; // bands: matrices M^(band_rows * 2^b), 64 columns each
+  const uint64_t *jump; // bands: matrices M^(band * band_rows) for band = 0, 1, ..., 64 columns each
   uint64_t *state_out;  // where final states go (== state unless banded)
 };
 
@@ -74,10 +74,12 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
 cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st);
 cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
                         cudaStream_t st);
-// state[s] := M^k applied to the state of stream s (from the hash when
-// from_hash), where M is the update's matrix over GF(2).
+// Columns of M^k, where M is the update's matrix over GF(2) (host side).
+void jump_matrix(uint64_t k, uint64_t *cols);
+// state[s] := the matrix with columns `cols` (64 words) applied to the state
+// of stream s (from the hash when from_hash).
 cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key, int from_hash,
-                        uint64_t k, cudaStream_t st);
+                        const uint64_t *cols, cudaStream_t st);
 // Values per thread of a generate-and-checksum launch over `span` streams
 // (vpt = 0: choose; else a power of two up to 64).
 uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device);
@@ -136,8 +138,10 @@ int batch_blocks_per_sm(uint32_t vpt, uint32_t block);
 // `checksum`: for the generate-and-checksum kernel instead of the row kernel.
 uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device,
                           bool checksum = false);
+// Most bands one banded launch is split into (one jump matrix each).
+constexpr uint32_t kMaxBands = 1024;
 // Host-side GF(2) tables for banded launches: writes `count` matrices
-// M^(band_rows * 2^b), b = 0 .. count-1, as 64 column words each.
+// M^(band * band_rows), band = 0 .. count-1, as 64 column words each.
 void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols);
 // Values per thread the work-list kernel is compiled for.
 bool batch_vpt_supported(uint32_t vpt);

@@ -128,25 +128,41 @@ __device__ __forceinline__ void store_tile_state(const uint64_t (&st)[VPT], uint
     }
 }
 
-// Advances the states by band * band_rows iterations: for each set bit b of
-// `band`, one multiplication over GF(2) by M^(band_rows * 2^b), whose 64
-// columns are jump[64 b .. 64 b + 63] (the same for every thread: broadcast
-// loads).  One state at a time, so the extra registers do not scale with VPT.
+// Nibble tables of a 64x64 matrix over GF(2) given by its columns (col[j] =
+// image of bit j): tab[q][e] = XOR of columns 4q+i over the bits i set in the
+// 4-bit value e.  The product with a vector is then 16 table reads and XORs
+// instead of 64 masked XORs, and each table is 16 words (128 bytes), so a
+// warp's reads of one table never conflict on the shared-memory banks.
+// Filled by the whole block.
+__device__ __forceinline__ void fill_jump_tables(uint64_t (*tab)[16], const uint64_t *__restrict__ cols) {
+  for (int idx = threadIdx.x; idx < 16 * 16; idx += blockDim.x) {
+    const int q = idx >> 4, e = idx & 15;
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc ^= cols[4 * q + i] & (0ull - static_cast<uint64_t>((e >> i) & 1));
+    tab[q][e] = acc;
+  }
+}
+
+__device__ __forceinline__ uint64_t apply_jump_tables(const uint64_t (*tab)[16], uint64_t x) {
+  uint64_t acc = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc ^= tab[q][(x >> (4 * q)) & 15];
+  return acc;
+}
+
+// Advances the states by band * band_rows iterations: one multiplication over
+// GF(2) by M^(band * band_rows), whose 64 columns are jump[64 band ..
+// 64 band + 63].  Called by every thread of the block (it synchronises the
+// block around refilling the shared tables).
 template <int VPT>
 __device__ __forceinline__ void jump_states(uint64_t (&st)[VPT], const uint64_t *__restrict__ jump,
-                                            uint64_t band) {
-  for (int b = 0; band; ++b, band >>= 1) {
-    if (!(band & 1)) continue;
-    const uint64_t *col = jump + 64 * b;
+                                            uint64_t band, uint64_t (*tab)[16]) {
+  __syncthreads();  // the previous unit's reads of the tables are done
+  fill_jump_tables(tab, jump + 64 * band);
+  __syncthreads();
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const uint64_t x = st[v];
-      uint64_t acc = 0;
-#pragma unroll 8
-      for (int j = 0; j < 64; ++j) acc ^= __ldg(col + j) & (0ull - ((x >> j) & 1ull));
-      st[v] = acc;
-    }
-  }
+  for (int v = 0; v < VPT; ++v) st[v] = apply_jump_tables(tab, st[v]);
 }
 
 // Row kernel.  Unbanded (BANDED = false): a work unit is a tile of BLOCK *
@@ -179,6 +195,7 @@ __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
       if (a.write_state) store_tile_state<VPT, W, BLOCK>(st, a.state, a, rel0, span);
     }
   } else {
+    __shared__ uint64_t jtab[16][16];
     const uint64_t band_rows = a.band_rows;
     const uint64_t n_bands = (a.rows + band_rows - 1) / band_rows;
     for (uint64_t w = blockIdx.x; w < n_tiles * n_bands; w += gridDim.x) {
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
       const uint64_t rel0 = tile * tile_vals;
       uint64_t st[VPT];
       load_tile<VPT, W, BLOCK>(st, a, rel0, span);
-      if (band) jump_states<VPT>(st, a.jump, band);
+      if (band) jump_states<VPT>(st, a.jump, band, jtab);  // band is the same for the whole block
       const uint64_t r0 = band * band_rows;
       const uint64_t rows = a.rows - r0 < band_rows ? a.rows - r0 : band_rows;
       uint64_t *out = a.out + r0 * a.pitch;
@@ -216,15 +233,17 @@ struct JumpMatrix {
   uint64_t col[64];
 };
 
+// The product goes through the nibble tables above, which each block fills
+// from the matrix (a kernel parameter).
 __global__ void jump_kernel(uint64_t *__restrict__ state, uint64_t n, uint64_t id_base, uint32_t key,
-                            int from_hash, const JumpMatrix m) {
+                            int from_hash, const __grid_constant__ JumpMatrix m) {
+  __shared__ uint64_t tab[16][16];
+  fill_jump_tables(tab, m.col);
+  __syncthreads();
   for (uint64_t s = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; s < n;
        s += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
     const uint64_t v = from_hash ? prng::initial_state(id_base + s, key) : state[s];
-    uint64_t acc = 0;
-#pragma unroll 16
-    for (int j = 0; j < 64; ++j) acc ^= m.col[j] & (0ull - ((v >> j) & 1ull));
-    state[s] = acc;
+    state[s] = apply_jump_tables(tab, v);
   }
 }
 
@@ -267,7 +286,10 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
     const uint64_t rel0 = tile * tile_vals;
     uint64_t st[VPT];
     load_tile<VPT, 1>(st, a, rel0, span);
-    if (BANDED && band) jump_states<VPT>(st, a.jump, band);
+    if constexpr (BANDED) {
+      __shared__ uint64_t jtab[16][16];
+      if (band) jump_states<VPT>(st, a.jump, band, jtab);  // band is the same for the whole block
+    }
     const uint64_t r0 = band * band_rows;
     const uint64_t rows = BANDED ? (a.rows - r0 < band_rows ? a.rows - r0 : band_rows) : a.rows;
     for (uint64_t r = 0; r < rows; ++r) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.h"
 #include "prng_math.cuh"
@@ -129,67 +130,102 @@ struct Gf2 {
   uint64_t col[64];
 };
 
-uint64_t gf2_apply(const Gf2 &m, uint64_t v) {
-  uint64_t acc = 0;
-  for (int j = 0; j < 64; ++j)
-    if ((v >> j) & 1) acc ^= m.col[j];
-  return acc;
-}
-
-Gf2 gf2_mul(const Gf2 &a, const Gf2 &b) {  // a * b: apply b first
+// a * b over GF(2) (apply b first).  Each column of b is multiplied through
+// byte tables of a: tab[q][e] = XOR of a's columns 8q+i over the bits i of
+// e, each entry one XOR from a smaller one, then 8 lookups per column.
+Gf2 gf2_mul(const Gf2 &a, const Gf2 &b) {
+  static thread_local uint64_t tab[8][256];
+  for (int q = 0; q < 8; ++q) {
+    tab[q][0] = 0;
+    for (int e = 1; e < 256; ++e) tab[q][e] = tab[q][e & (e - 1)] ^ a.col[8 * q + __builtin_ctz(e)];
+  }
   Gf2 r;
-  for (int j = 0; j < 64; ++j) r.col[j] = gf2_apply(a, b.col[j]);
+  for (int j = 0; j < 64; ++j) {
+    uint64_t acc = 0;
+    for (int q = 0; q < 8; ++q) acc ^= tab[q][(b.col[j] >> (8 * q)) & 255];
+    r.col[j] = acc;
+  }
   return r;
 }
 
-// M^k for the xorshift update: columns of M are the update of each unit
-// vector; the power by repeated squaring.
+Gf2 gf2_identity() {
+  Gf2 r;
+  for (int j = 0; j < 64; ++j) r.col[j] = uint64_t(1) << j;
+  return r;
+}
+
+// M^(2^i), i = 0 .. 63, for the xorshift update M (columns of M are the
+// update of each unit vector), built once by repeated squaring.
+const Gf2 *update_powers_of_two() {
+  static const std::vector<Gf2> pw = [] {
+    std::vector<Gf2> v(64);
+    for (int j = 0; j < 64; ++j) v[0].col[j] = prng::xorshift_update(uint64_t(1) << j);
+    for (int i = 1; i < 64; ++i) v[i] = gf2_mul(v[i - 1], v[i - 1]);
+    return v;
+  }();
+  return pw.data();
+}
+
+// M^k: one product per set bit of k.
 Gf2 update_power(uint64_t k) {
-  Gf2 base, result;
-  for (int j = 0; j < 64; ++j) {
-    base.col[j] = prng::xorshift_update(uint64_t(1) << j);
-    result.col[j] = uint64_t(1) << j;
-  }
-  while (k) {
-    if (k & 1) result = gf2_mul(base, result);
-    base = gf2_mul(base, base);
-    k >>= 1;
-  }
+  const Gf2 *pw = update_powers_of_two();
+  Gf2 result = gf2_identity();
+  for (int i = 0; k; ++i, k >>= 1)
+    if (k & 1) result = gf2_mul(pw[i], result);
   return result;
 }
 
 }  // namespace
 
 void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols) {
-  Gf2 m = update_power(band_rows);
+  const Gf2 step = update_power(band_rows);
+  Gf2 m = gf2_identity();  // band 0 starts at the launch's first row
   for (uint32_t b = 0; b < count; ++b) {
     for (int j = 0; j < 64; ++j) cols[64 * b + j] = m.col[j];
-    m = gf2_mul(m, m);
+    m = gf2_mul(step, m);
   }
 }
 
-// Bands only when the tiles cannot cover half the SMs (128 unbanded tiles of
-// 2^16 streams ran at 7.37 TB/s, three bands of them at 6.25); then about
-// two (tile, band) units per SM (16 tiles of 4096 streams: 19 bands 6.6 TB/s,
-// 10 bands 4.7 TB/s).
+// Row kernel (bound by HBM writes): bands only when the tiles cannot cover
+// half the SMs (128 unbanded tiles of 2^16 streams ran at 7.37 TB/s, three
+// bands of them at 6.25); then about two (tile, band) units per SM (16 tiles
+// of 4096 streams: 19 bands 6.6 TB/s, 10 bands 4.7 TB/s).
+// Checksum kernel (bound by integer issue): bands whenever the tiles leave
+// resident block slots empty, up to about four units per slot, so that the
+// last wave of units is a small part of the launch.
+// Bands hold at least 128 rows, which amortises each unit's jump.
 uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device, bool checksum) {
   const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
   const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
-  const uint64_t target = 2 * sms;            // units wanted in flight
-  const uint64_t min_band = 128;              // rows per band: amortises the jump
-  if (tiles * 2 >= sms || rows < 2 * min_band) return 0;
-  const bool have = checksum ? checksum_kernel_fn(sh.vpt, true) != nullptr
-                             : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true) != nullptr;
-  if (!have) return 0;  // no banded variant of this shape
+  const uint64_t min_band = 128;
+  const void *fn = checksum ? checksum_kernel_fn(sh.vpt, true)
+                            : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true);
+  if (!fn || rows < 2 * min_band) return 0;  // no banded variant of this shape, or too few rows
+  uint64_t target;
+  if (checksum) {
+    const uint64_t slots = sms * static_cast<uint64_t>(std::max(1, occupancy(fn, sh.block)));
+    if (tiles >= slots) return 0;
+    target = 4 * slots;
+  } else {
+    if (tiles * 2 >= sms) return 0;
+    target = 2 * sms;
+  }
   uint64_t bands = (target + tiles - 1) / tiles;
   if (bands > rows / min_band) bands = rows / min_band;
+  if (bands > kMaxBands) bands = kMaxBands;
   if (bands < 2) return 0;
   return (rows + bands - 1) / bands;
 }
 
+void jump_matrix(uint64_t k, uint64_t *cols) {
+  const Gf2 m = update_power(k);
+  for (int j = 0; j < 64; ++j) cols[j] = m.col[j];
+}
+
 cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key, int from_hash,
-                        uint64_t k, cudaStream_t st) {
-  Gf2 m = update_power(k);
+                        const uint64_t *cols, cudaStream_t st) {
+  Gf2 m;
+  for (int j = 0; j < 64; ++j) m.col[j] = cols[j];
   int dev = 0;
   cudaGetDevice(&dev);
   const uint64_t blocks_needed = (n + 255) / 256;
