@@ -362,11 +362,12 @@ def run_gpu(args, wl):
             step_host_checksum()
         barrier()
         hc_s = max_over_ranks(time.perf_counter() - t0)
+        hc_stats = gh.host_stats()
         gh.close()
         e2e["host_checksum"] = {"value": nbytes * ws * args.e2e_steps / hc_s / 1e9, "unit": "GB/s",
                                 "ms_per_step": 1e3 * hc_s / args.e2e_steps,
                                 "consumers": "default (host cores but one, 1-16)",
-                                "host_cores": os.cpu_count()}
+                                "host_cores": os.cpu_count(), "last_step": hc_stats}
 
         # The paper's program as measured there: every value to stdout, here
         # /dev/null, through the staging slots and one writer thread.
@@ -386,10 +387,11 @@ def run_gpu(args, wl):
             step_fd()
         barrier()
         fd_s = max_over_ranks(time.perf_counter() - t0)
+        fd_stats = gf.host_stats()
         os.close(fd)
         gf.close()
         e2e["stdout_devnull"] = {"value": nbytes * ws * args.e2e_steps / fd_s / 1e9, "unit": "GB/s",
-                                 "ms_per_step": 1e3 * fd_s / args.e2e_steps}
+                                 "ms_per_step": 1e3 * fd_s / args.e2e_steps, "last_step": fd_stats}
 
     gen.close()
     if rank != 0:

@@ -209,6 +209,29 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink,
  * Blocks until everything is written; RNG_ESINK if a write fails. */
 int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err);
 
+/* Timing of the host side of the last call that went through the double
+ * buffer (rng_generate with host output on the double-buffer path,
+ * rng_generate_sink, rng_generate_fd, rng_generate_host_checksum): which
+ * stage bounds the pipeline.  A large producer_wait_s means the consumers
+ * are behind (every slot held); a large copy_wait_s means the consumers
+ * wait for the link.  Zero consumers and slots: the destination was
+ * page-locked and the copies went straight into it. */
+typedef struct rng_host_stats {
+    uint64_t chunks;          /* device-buffer chunks streamed */
+    uint32_t consumers;       /* host consumer threads */
+    uint32_t slots;           /* pinned staging slots */
+    double wall_s;            /* the call, from its first launch to its end */
+    double producer_wait_s;   /* issuing thread waiting for a free slot */
+    double copy_wait_s;       /* consumers waiting for their slot's copy,
+                                 summed over the consumer threads */
+    double consume_s;         /* consumers copying, folding or in the sink,
+                                 summed over the consumer threads */
+} rng_host_stats;
+
+/* Copies the host-side timing of g's last double-buffer call into *out.
+ * RNG_EINVAL for NULL arguments. */
+int rng_host_stats_get(const rng_gen *g, rng_host_stats *out);
+
 /* Host-side check of streamed output (the consumer of the paper's streaming
  * program, Section 5, "out" block): streams iterations p .. p+iterations-1
  * over the host link through the double buffer and the pinned staging slots,

@@ -49,6 +49,18 @@ class RngOpts(ctypes.Structure):
     ]
 
 
+class RngHostStats(ctypes.Structure):
+    _fields_ = [
+        ("chunks", c_u64),
+        ("consumers", c_u32),
+        ("slots", c_u32),
+        ("wall_s", ctypes.c_double),
+        ("producer_wait_s", ctypes.c_double),
+        ("copy_wait_s", ctypes.c_double),
+        ("consume_s", ctypes.c_double),
+    ]
+
+
 class RngBatchOpts(ctypes.Structure):
     _fields_ = [
         ("struct_size", c_u32),
@@ -100,6 +112,7 @@ SIGNATURES = {
     "rng_generate_ring": ([c_vp, c_u64, c_vp, c_u64, P_err], c_int),
     "rng_generate_fd": ([c_vp, c_u64, c_int, P_err], c_int),
     "rng_generate_host_checksum": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
+    "rng_host_stats_get": ([c_vp, c_vp], c_int),
     "rng_generate_checksum": ([c_vp, c_u64, c_vp, c_vp, P_err], c_int),
     "rng_skip": ([c_vp, c_u64, P_err], c_int),
     "rng_position": ([c_vp, P_u64], c_int),

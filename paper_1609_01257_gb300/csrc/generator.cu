@@ -78,6 +78,7 @@ struct rng_gen {
   std::chrono::steady_clock::time_point wall0;
   rng_prof *prof = nullptr;
   std::string summary;
+  rng_host_stats host_stats{};  // of the last call through the staging slots
 };
 
 namespace {
@@ -327,13 +328,23 @@ struct Consumer {
   int status = RNG_OK;
   std::string msg;
   std::vector<std::thread> th;
+  double copy_wait_s = 0.0, consume_s = 0.0;  // summed over threads (under mu)
 
-  int consume(const Job &j, std::string *m) {
+  int consume(const Job &j, std::string *m, double *wait_s, double *work_s) {
+    const auto t0 = std::chrono::steady_clock::now();
     cudaError_t st = cudaEventSynchronize(g->slot_ready[j.slot]);
+    const auto t1 = std::chrono::steady_clock::now();
+    *wait_s = std::chrono::duration<double>(t1 - t0).count();
     if (st != cudaSuccess) {
       *m = std::string("cudaEventSynchronize: ") + cudaGetErrorString(st);
       return RNG_ECUDA;
     }
+    const int rc = consume_ready(j, m);
+    *work_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+    return rc;
+  }
+
+  int consume_ready(const Job &j, std::string *m) {
     const uint64_t *vals = static_cast<const uint64_t *>(g->h_slots[j.slot]);
     if (t.out_host) {
       memcpy(t.out_host + j.c.r0 * g->n + j.c.s0, vals, j.c.rows * j.c.span * 8);
@@ -371,9 +382,12 @@ struct Consumer {
         skip = status != RNG_OK;
       }
       std::string m;
-      const int rc = skip ? RNG_OK : consume(j, &m);
+      double wait_s = 0.0, work_s = 0.0;
+      const int rc = skip ? RNG_OK : consume(j, &m, &wait_s, &work_s);
       {
         std::lock_guard<std::mutex> lk(mu);
+        copy_wait_s += wait_s;
+        consume_s += work_s;
         if (rc != RNG_OK && status == RNG_OK) {
           status = rc;
           msg = m;
@@ -436,6 +450,8 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
     }
   }
   const auto wait_limit = std::chrono::milliseconds(g->opts.host_wait_ms ? g->opts.host_wait_ms : 600000);
+  const auto call0 = std::chrono::steady_clock::now();
+  double producer_wait_s = 0.0;
 
   int status = RNG_OK;
   std::string status_msg;
@@ -444,11 +460,13 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
     const int b = static_cast<int>(c & 1);
     size_t slot = 0;
     if (staged) {
+      const auto w0 = std::chrono::steady_clock::now();
       std::unique_lock<std::mutex> lk(cons.mu);
       const bool ok = cons.cv.wait_for(lk, wait_limit, [&] {
         return cons.status != RNG_OK ||
                std::find(cons.slot_free.begin(), cons.slot_free.end(), true) != cons.slot_free.end();
       });
+      producer_wait_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
       if (cons.status != RNG_OK) break;
       if (!ok) {
         status = RNG_ETIMEOUT;
@@ -497,6 +515,15 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
   }
   cudaError_t st = cudaStreamSynchronize(g->copy);
   cudaError_t st2 = cudaStreamSynchronize(g->compute);
+  rng_host_stats &hs = g->host_stats;
+  hs = rng_host_stats{};
+  hs.chunks = chunks.size();
+  hs.consumers = staged ? static_cast<uint32_t>(cons.th.size()) : 0;
+  hs.slots = staged ? static_cast<uint32_t>(slots) : 0;
+  hs.wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - call0).count();
+  hs.producer_wait_s = producer_wait_s;
+  hs.copy_wait_s = cons.copy_wait_s;
+  hs.consume_s = cons.consume_s;
   if (status == RNG_OK && st != cudaSuccess) status = rngi::cuda_fail(err, st, "cudaStreamSynchronize(copy)");
   if (status == RNG_OK && st2 != cudaSuccess) status = rngi::cuda_fail(err, st2, "cudaStreamSynchronize(compute)");
   if (status != RNG_OK) {
@@ -903,6 +930,12 @@ int rng_skip(rng_gen *g, uint64_t iterations, rng_err **err) {
   if (rc) return rc;
   g->materialized = true;
   g->pos += iterations;  // wraps modulo 2^64 like the period of the update
+  return RNG_OK;
+}
+
+int rng_host_stats_get(const rng_gen *g, rng_host_stats *out) {
+  if (!g || !out) return RNG_EINVAL;
+  *out = g->host_stats;
   return RNG_OK;
 }
 

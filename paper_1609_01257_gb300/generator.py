@@ -203,6 +203,14 @@ class Generator:
                     ctypes.c_void_p(row_xor.ctypes.data), ctypes.c_void_p(row_sum.ctypes.data))
         return row_xor, row_sum
 
+    def host_stats(self) -> dict:
+        """Host-side timing of the last double-buffer call: chunks, consumer
+        threads, slots, wall time, the issuing thread's wait for free slots,
+        the consumers' wait for copies and their consuming time (seconds)."""
+        s = C.RngHostStats()
+        self._lib.rng_host_stats_get(self._h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in C.RngHostStats._fields_}
+
     def generate_fd(self, iterations: int, fd: int):
         """Stream ``iterations`` rows as raw uint64 values to file descriptor ``fd``."""
         C.check(self._lib.rng_generate_fd, self._h, iterations, fd)

@@ -114,3 +114,41 @@ def test_host_consumers_bound():
     with pytest.raises(rng.RngError) as e:
         rng.Generator(16, 1, host_consumers=65)
     assert e.value.code == 1
+
+
+def test_host_stats_show_a_slow_consumer():
+    # A sink slower than the link: the issuing thread spends most of the call
+    # waiting for free slots, and the consumer's time covers the sleeps.
+    import time
+    n, T = 4096, 12
+    g = rng.Generator(n, 2, device_buffer_bytes=8 * n * 2)
+
+    def slow(first_it, block, first_stream):
+        time.sleep(0.02)
+
+    g.generate_sink(T, slow)
+    s = g.host_stats()
+    g.close()
+    assert s["chunks"] == 6 and s["consumers"] == 1 and s["slots"] == 3
+    assert s["consume_s"] >= 6 * 0.02 * 0.9
+    assert s["producer_wait_s"] > 0.5 * s["wall_s"] and s["wall_s"] >= s["consume_s"] * 0.9
+
+
+def test_host_stats_of_a_fold_and_of_a_page_locked_copy():
+    import torch
+    n, T = 8192, 10
+    g = rng.Generator(n, 2, device_buffer_bytes=8 * n, host_consumers=4)
+    g.generate_host_checksum(T)
+    s = g.host_stats()
+    assert s["chunks"] == T and s["consumers"] == 4 and s["slots"] == 6
+    assert s["wall_s"] > 0 and s["consume_s"] > 0 and s["copy_wait_s"] >= 0
+    g.close()
+    # Page-locked destination on the double buffer: copies land in place, no
+    # staging slots and no consumer threads.
+    host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
+    g = rng.Generator(n, 2, device_buffer_bytes=8 * n * 5, host_path=1)
+    g.generate_to_host(T, host)
+    s = g.host_stats()
+    g.close()
+    assert s["chunks"] == 2 and s["consumers"] == 0 and s["slots"] == 0
+    assert np.array_equal(host.numpy(), oracle.generate(n, 2, T))
