@@ -33,15 +33,20 @@ int device_sm_count(int device) {
 }
 
 // Values per thread for 256-thread blocks, from sweeps of the row kernel on
-// GB300 (152 SMs) writing 16-32 GiB per point with one tile per block: 24
-// streams per thread (one 48 KiB run per block and row, one resident block
-// per SM) was fastest from 2^22 to 2^26 streams and 12 around 2^21.  Below
-// that, the fastest shapes made about 128 tiles (one long-running block on
-// most SMs): 32 at 2^20, 8 at 2^18, 2 at 2^16.
+// GB300 (152 SMs) writing 4-32 GiB per launch with one tile per block:
+//  - 24 streams per thread (one 48 KiB run per block and row, one resident
+//    block per SM) was fastest from 2^22 to 2^26 streams;
+//  - from 2^20 up to that, one stream per thread (thousands of short tiles):
+//    7.14-7.23 TB/s at 2^20 and 7.33-7.38 at 2^21 on every GPU tried, where
+//    shapes of about 128 tiles (fewer blocks than SMs) ran at 7.4 TB/s on some
+//    GPUs but 6.1 on others;
+//  - below 2^20 about 128 tiles (one long-running block on most SMs) stayed
+//    fastest on average: 8 per thread at 2^18 (6.3-7.6 TB/s against 6.5 for
+//    one per thread), 2 at 2^16 (6.2-7.4 against 6.5).
 uint32_t default_vpt(uint64_t streams, int sms) {
   const uint64_t M = uint64_t(1) << 20;
   if (streams >= 7 * M / 2) return 24;
-  if (streams >= 3 * M / 2) return 12;
+  if (streams >= M) return 1;
   (void)sms;
   const uint64_t v = streams / (uint64_t(kGenBlock) * 128);
   for (uint32_t c : {32u, 16u, 8u, 4u, 2u})
