@@ -341,6 +341,13 @@ def run_gpu(args, wl):
             "profiled_step": {"read_buffer_s": prof["aggregate"].get("READ_BUFFER", (0, 0))[0],
                               "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0],
                               "overlap_s": sum(prof["overlaps"].values())}}
+        # The same double buffer with its reads done by a copy kernel.
+        gsm = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+                            host_path=3, profiling=False, init=False)
+        sm_s, _ = host_leg(gsm, args.e2e_steps)
+        gsm.close()
+        e2e["double_buffer_copy_kernel"] = {"value": nbytes * ws * args.e2e_steps / sm_s / 1e9, "unit": "GB/s",
+                                            "ms_per_step": 1e3 * sm_s / args.e2e_steps}
         e2e["host_link_GBps"] = link
         e2e["frac_link"] = e2e["value"] / link
         del host

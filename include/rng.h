@@ -110,7 +110,14 @@ typedef struct rng_opts {
                                      NVLink-C2C), else double buffer;
                                      1 = always the double buffer of Section 5;
                                      2 = always direct (RNG_EINVAL if the GPU
-                                     cannot store into the destination) */
+                                     cannot store into the destination);
+                                     3 = the double buffer with its reads done
+                                     by a copy kernel on the copy stream (SMs
+                                     storing into page-locked memory or the
+                                     staging slots) instead of the copy engine.
+                                     Sinks, file descriptors and host checksums
+                                     use the double buffer in every mode, with
+                                     copy-kernel reads in mode 3 */
     uint32_t host_consumers;      /* host threads draining the staging slots
                                      (at most 64).  0 (default): one for sinks
                                      (in order); for pageable copies and host

@@ -68,6 +68,7 @@ struct rng_gen {
   uint64_t *d_buf[2] = {nullptr, nullptr};
   size_t buf_bytes = 0;
   std::vector<void *> h_slots;
+  std::vector<void *> h_slots_dev;  // the slots' device-side addresses
   std::vector<cudaEvent_t> slot_ready;
   cudaEvent_t produced[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
   // profiling
@@ -224,7 +225,13 @@ int ensure_buffers(rng_gen *g, size_t slots, rng_err **err) {
       cudaFreeHost(p);
       return rc;
     }
+    void *pd = nullptr;
+    if (cudaHostGetDevicePointer(&pd, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      pd = p;  // unified addressing: the host address is valid on the device
+    }
     g->h_slots.push_back(p);
+    g->h_slots_dev.push_back(pd);
     g->slot_ready.push_back(e);
   }
   return RNG_OK;
@@ -282,6 +289,7 @@ struct Target {
   uint64_t *row_xor = nullptr;   // or fold it into per-row XOR / sum
   uint64_t *row_sum = nullptr;
   unsigned consumers = 1;        // host threads draining the slots
+  bool sm_copy = false;          // reads by a copy kernel instead of the copy engine
 };
 
 // XOR and wrapping sum of `n` values; four independent lanes so that the
@@ -410,10 +418,13 @@ unsigned auto_consumers() {
 
 int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
   bool pinned = false;
+  uint64_t *out_dev_addr = tgt.out_host;  // the destination as the device addresses it
   if (tgt.out_host) {
     cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, tgt.out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost)
+    if (cudaPointerGetAttributes(&attr, tgt.out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost) {
       pinned = true;
+      if (attr.devicePointer) out_dev_addr = static_cast<uint64_t *>(attr.devicePointer);
+    }
     cudaGetLastError();
   }
   const bool staged = !pinned;
@@ -486,9 +497,14 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
     st = cudaEventRecord(g->produced[b], g->compute);
     if (st == cudaSuccess) st = cudaStreamWaitEvent(g->copy, g->produced[b], 0);
     if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "event ordering"); break; }
-    void *dst = staged ? g->h_slots[slot] : static_cast<void *>(tgt.out_host + ck.r0 * g->n + ck.s0);
     long op = op_begin(g, "READ_BUFFER", kQueueComms, g->copy);
-    st = cudaMemcpyAsync(dst, g->d_buf[b], ck.rows * ck.span * 8, cudaMemcpyDeviceToHost, g->copy);
+    if (tgt.sm_copy) {
+      void *dst = staged ? g->h_slots_dev[slot] : static_cast<void *>(out_dev_addr + ck.r0 * g->n + ck.s0);
+      st = rngi::launch_copy(static_cast<uint64_t *>(dst), g->d_buf[b], ck.rows * ck.span, g->copy);
+    } else {
+      void *dst = staged ? g->h_slots[slot] : static_cast<void *>(tgt.out_host + ck.r0 * g->n + ck.s0);
+      st = cudaMemcpyAsync(dst, g->d_buf[b], ck.rows * ck.span * 8, cudaMemcpyDeviceToHost, g->copy);
+    }
     op_end(g, op, g->copy);
     if (st == cudaSuccess) st = cudaEventRecord(g->copied[b], g->copy);
     if (st == cudaSuccess && staged) st = cudaEventRecord(g->slot_ready[slot], g->copy);
@@ -641,7 +657,7 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   if (o.device_buffer_bytes < 16 || o.device_buffer_bytes % 16)
     return rngi::fail(err, RNG_EINVAL, "rng_create: device_buffer_bytes must be a positive multiple of 16");
   if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
-  if (o.host_path > 2) return rngi::fail(err, RNG_EINVAL, "rng_create: host_path must be 0, 1 or 2");
+  if (o.host_path > 3) return rngi::fail(err, RNG_EINVAL, "rng_create: host_path must be 0, 1, 2 or 3");
   if (o.host_consumers > 64) return rngi::fail(err, RNG_EINVAL, "rng_create: host_consumers must be at most 64");
   if (o.store_width != 0 && o.store_width != 1 && o.store_width != 2 && o.store_width != 4)
     return rngi::fail(err, RNG_EINVAL, "rng_create: store_width must be 0, 1, 2 or 4");
@@ -740,13 +756,14 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   if (rc) return rc;
   if (out_host) {
     uint64_t *dptr = nullptr;
-    const bool can = g->opts.host_path != 1 && device_can_store(g, out_host, &dptr);
+    const bool can = (g->opts.host_path == 0 || g->opts.host_path == 2) && device_can_store(g, out_host, &dptr);
     if (g->opts.host_path == 2 && !can)
       return rngi::fail(err, RNG_EINVAL, "rng_generate: the GPU cannot store into this host memory (host_path = 2)");
     if (can) return direct_host(g, iterations, dptr, err);
     Target tgt;
     tgt.out_host = out_host;
     tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : auto_consumers();
+    tgt.sm_copy = g->opts.host_path == 3;
     return double_buffer_host(g, iterations, tgt, err);
   }
   if (reinterpret_cast<uintptr_t>(out_dev) % 8)
@@ -810,6 +827,7 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink, void *u
   tgt.sink = sink;
   tgt.user = user;
   tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : 1;
+  tgt.sm_copy = g->opts.host_path == 3;
   return double_buffer_host(g, iterations, tgt, err);
 }
 
@@ -845,6 +863,7 @@ int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err) {
   tgt.sink = fd_sink;
   tgt.user = &user;
   tgt.consumers = 1;  // the bytes must reach the descriptor in order
+  tgt.sm_copy = g->opts.host_path == 3;
   return double_buffer_host(g, iterations, tgt, err);
 }
 
@@ -865,6 +884,7 @@ int rng_generate_host_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xo
   tgt.row_xor = row_xor_host;
   tgt.row_sum = row_sum_host;
   tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : auto_consumers();
+  tgt.sm_copy = g->opts.host_path == 3;
   return double_buffer_host(g, iterations, tgt, err);
 }
 

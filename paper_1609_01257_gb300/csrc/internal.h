@@ -23,6 +23,7 @@ const void *worklist_kernel_fn(uint32_t vpt);
 const void *batch_work_kernel_fn(uint32_t vpt);
 const void *init_kernel_fn();
 const void *jump_kernel_fn();
+const void *copy_kernel_fn();
 
 // Sets *err (when err != NULL and *err == NULL) and returns `code`.
 int fail(rng_err **err, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -74,6 +75,9 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
 cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st);
 cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
                         cudaStream_t st);
+// n words from device memory `src` to page-locked host memory `dst` (a
+// device-side address) by SMs, on stream st.
+cudaError_t launch_copy(uint64_t *dst, const uint64_t *src, uint64_t n, cudaStream_t st);
 // Columns of M^k, where M is the update's matrix over GF(2) (host side).
 void jump_matrix(uint64_t k, uint64_t *cols);
 // state[s] := the matrix with columns `cols` (64 words) applied to the state

@@ -247,6 +247,24 @@ __global__ void jump_kernel(uint64_t *__restrict__ state, uint64_t n, uint64_t i
   }
 }
 
+// Device-to-host read of one double-buffer chunk done by SMs instead of the
+// copy engine: n words from a device buffer into page-locked host memory
+// (addressed from the device), four independent loads in flight per thread,
+// streaming stores.
+__global__ void copy_kernel(uint64_t *__restrict__ dst, const uint64_t *__restrict__ src, uint64_t n) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    const uint64_t a = __ldcs(src + i), b = __ldcs(src + i + stride);
+    const uint64_t c = __ldcs(src + i + 2 * stride), d = __ldcs(src + i + 3 * stride);
+    store_one<kPolicyStreaming>(dst + i, a);
+    store_one<kPolicyStreaming>(dst + i + stride, b);
+    store_one<kPolicyStreaming>(dst + i + 2 * stride, c);
+    store_one<kPolicyStreaming>(dst + i + 3 * stride, d);
+  }
+  for (; i < n; i += stride) store_one<kPolicyStreaming>(dst + i, __ldcs(src + i));
+}
+
 // 64-bit XOR and wrapping sum across a warp with 32-bit reductions: the sum
 // is split into two 16-bit low parts (no carry can be lost over 32 lanes)
 // and the high word, whose sum only matters modulo 2^32.
@@ -591,5 +609,6 @@ const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }
 const void *batch_work_kernel_fn(uint32_t vpt) { return select_batch_work(vpt); }
 const void *init_kernel_fn() { return reinterpret_cast<const void *>(&init_kernel); }
 const void *jump_kernel_fn() { return reinterpret_cast<const void *>(&jump_kernel); }
+const void *copy_kernel_fn() { return reinterpret_cast<const void *>(&copy_kernel); }
 
 }  // namespace rngi

@@ -26,9 +26,10 @@ CASES = [
 
 
 @pytest.mark.parametrize("n,T,buf", CASES)
-@pytest.mark.parametrize("consumers", [1, 3, 8])
-def test_host_checksum_matches_oracle(n, T, buf, consumers):
-    g = rng.Generator(n, 21, device_buffer_bytes=buf, host_consumers=consumers)
+@pytest.mark.parametrize("consumers,host_path", [(1, 0), (3, 0), (8, 0), (3, 3)])
+def test_host_checksum_matches_oracle(n, T, buf, consumers, host_path):
+    # host_path 3: the slots are filled by a copy kernel instead of the copy engine.
+    g = rng.Generator(n, 21, device_buffer_bytes=buf, host_consumers=consumers, host_path=host_path)
     rx, rs = g.generate_host_checksum(T)
     tail = g.generate(2).cpu().numpy()  # the streams advanced by T
     g.close()
@@ -85,23 +86,24 @@ def test_concurrent_sink_sees_every_chunk_once():
     assert np.array_equal(got, oracle.generate(n, 6, T))
 
 
-@pytest.mark.parametrize("consumers", [1, 4])
-def test_pageable_copy_with_consumers(consumers):
+@pytest.mark.parametrize("consumers,host_path", [(1, 1), (4, 1), (4, 3)])
+def test_pageable_copy_with_consumers(consumers, host_path):
     # Double buffer into pageable memory: copies out of the staging slots
     # are spread over the consumer threads.
     n, T = 70_001, 9
-    g = rng.Generator(n, 8, device_buffer_bytes=8 * 20_000, host_path=1, host_consumers=consumers)
+    g = rng.Generator(n, 8, device_buffer_bytes=8 * 20_000, host_path=host_path, host_consumers=consumers)
     out = np.zeros((T, n), dtype=np.uint64)
     g.generate_to_host(T, out)
     g.close()
     assert np.array_equal(out, oracle.generate(n, 8, T))
 
 
-def test_fd_output_in_order_with_consumers(tmp_path):
+@pytest.mark.parametrize("host_path", [0, 3])
+def test_fd_output_in_order_with_consumers(tmp_path, host_path):
     # rng_generate_fd keeps one consumer whatever host_consumers says: the
     # bytes reach the file in stream order.
     n, T = 5000, 12
-    g = rng.Generator(n, 4, device_buffer_bytes=8 * n, host_consumers=6)
+    g = rng.Generator(n, 4, device_buffer_bytes=8 * n, host_consumers=6, host_path=host_path)
     path = tmp_path / "out.bin"
     with open(path, "wb") as f:
         g.generate_fd(T, f.fileno())

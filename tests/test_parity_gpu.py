@@ -173,13 +173,14 @@ def test_no_write_outside_output():
     assert np.array_equal(r[pad:-pad].view(np.uint64).reshape(T, n), oracle.generate(n, 8, T))
 
 
-@pytest.mark.parametrize("host_path", [0, 1])
+@pytest.mark.parametrize("host_path", [0, 1, 3])
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("n,T,buf", [(4096, 40, 1 << 16), (3001, 7, 8 * 3001 * 2), (5000, 3, 4096), (7, 100, 64)])
 def test_host_output(host_path, pinned, n, T, buf):
     # host_path 1: the double buffer; buf smaller than one row (5000 streams x
-    # 8 B > 4096) exercises column slabs.  host_path 0: direct stores where
-    # the GPU can reach the destination.
+    # 8 B > 4096) exercises column slabs.  host_path 3: the same with the
+    # reads done by a copy kernel (odd widths: 8-byte aligned destinations).
+    # host_path 0: direct stores where the GPU can reach the destination.
     g = rng.Generator(n, 4, device_buffer_bytes=buf, host_path=host_path)
     out = torch.empty((T, n), dtype=torch.uint64)
     if pinned:
@@ -194,7 +195,7 @@ def test_host_output(host_path, pinned, n, T, buf):
     assert np.array_equal(second, want[T:])
 
 
-@pytest.mark.parametrize("host_path", [0, 1])
+@pytest.mark.parametrize("host_path", [0, 1, 3])
 def test_device_then_host_then_device(host_path):
     g = rng.Generator(2048, 9, device_buffer_bytes=8 * 2048 * 3, host_path=host_path)
     a = g.generate(4).cpu().numpy()
@@ -348,7 +349,7 @@ def test_checksum_mode_banded(n, T):
     assert np.array_equal(tail, oracle.generate(n, 31, 2, p0=T))
 
 
-@pytest.mark.parametrize("host_path", [1, 2])
+@pytest.mark.parametrize("host_path", [1, 2, 3])
 def test_few_streams_many_rows_to_host(host_path):
     n, T = 1000, 3000
     g = rng.Generator(n, 23, host_path=host_path)

@@ -46,6 +46,26 @@ def test_streaming_full_size_sampled_rows_and_checksums():
     assert prof["aggregate"]["READ_BUFFER"][0] > prof["aggregate"]["RNG_KERNEL"][0]
 
 
+def test_copy_kernel_double_buffer_full_size():
+    # The double buffer with its reads done by a copy kernel (host_path 3),
+    # into the same 32 GiB of page-locked memory.
+    cfg = workloads.STREAMING
+    n, T, seed = cfg["streams"], cfg["iterations"], cfg["seed"]
+    host = torch.empty((T, n), dtype=torch.uint64).pin_memory()
+    g = rng.Generator(n, seed, device_buffer_bytes=cfg["device_buffer_bytes"], host_path=3)
+    g.generate_to_host(T, host)
+    cnt_r, _ = g.profile_stat("READ_BUFFER")
+    g.close()
+    out = host.numpy()
+    wx, ws, samples = oracle.row_checksums(n, seed, T, sample_every=64)
+    for j, i in enumerate(range(0, T, 64)):
+        assert np.array_equal(out[i], samples[j]), f"row {i} differs"
+    for i0 in range(0, T, 64):
+        x, s = _row_checksums(out[i0:i0 + 64])
+        assert np.array_equal(x, wx[i0:i0 + 64]) and np.array_equal(s, ws[i0:i0 + 64]), i0
+    assert cnt_r == T
+
+
 def test_direct_to_host_full_size_checksums():
     # The same run with the kernel storing straight into host memory.
     cfg = workloads.STREAMING
