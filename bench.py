@@ -410,7 +410,8 @@ def run_gpu(args, wl):
     achieved = nbytes / k_avg / 1e9
     traffic = _traffic_per_launch(args.workload)
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "GB/s", "values_per_s": value * 1e9 / 8, "n_gpus": ws,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl["name"], "streams_per_gpu": n, "iterations": T, "seed": seed,
@@ -782,6 +783,12 @@ def run_sweep(args):
 
         for vpt in args.sweep_vpts:
             res[vpt], res_dram[vpt], _ = point(values_per_thread=vpt)
+        cpu = None
+        if n <= (1 << 18) and not args.skip_cpu_baseline:
+            # The oracle on the same point (small stream counts): one launch's rows.
+            nb, dt = cpu_oracle_sample(n, 1, rows)
+            cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "values_per_s": nb / 8 / dt, "cores": 1,
+                   "kind": "oracle", "sample": f"{n} streams x {rows} iterations, single-threaded C oracle, {dt:.1f} s"}
         dflt, dflt_dram, cfg = point()
         ck = rng.Generator(n, 1, init=False)
         ck.init()
@@ -797,6 +804,7 @@ def run_sweep(args):
                     "dram_GBps_incl_state_by_vpt": {str(k): round(v, 1) for k, v in res_dram.items()},
                     "default_shape": {"vpt": cfg[0], "grid": cfg[2], "GBps": round(dflt, 1),
                                       "dram_GBps_incl_state": round(dflt_dram, 1)},
+                    "cpu_baseline": cpu,
                     "checksum_iterations": T, "checksum_values_per_s": n * T / t,
                     "checksum_equiv_GBps": 8 * n * T / t / 1e9})
     return 0
