@@ -5,8 +5,14 @@
 // buffers between launches.  Here one launch covers many iterations: each
 // thread keeps its streams' states in registers for the whole launch and
 // writes one row (iteration) after another in the iteration-major layout,
-// with warp-contiguous 16-byte stores.  Nothing is read per value; the
-// state array is touched once at the start and once at the end.
+// each warp store covering a contiguous run (one 8-byte streaming store per
+// value from six streams per thread up, 16- or 32-byte vector stores below).
+// Nothing is read per value; the state array is touched once at the start
+// and once at the end.
+//
+// Also here: the generate-and-checksum kernel, the work-list kernels of the
+// batched, served and allocation-free forms, the init and jump-ahead kernels,
+// and the copy kernel of the double buffer's copy-kernel reads.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -1,6 +1,7 @@
-// Host-side launch code of the generation kernels: shape selection (values
-// per thread, store width, grid) and the launches themselves.  The kernels
-// are in kernels.cu; this file holds no device code.
+// Host-side launch code of the kernels: shape selection (values per thread,
+// store width, grid, bands), the GF(2) jump matrices of rng_skip and of
+// banded launches, and the launches themselves.  The kernels are in
+// kernels.cu; this file holds no device code.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
