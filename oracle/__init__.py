@@ -68,6 +68,11 @@ class OracleLib:
             "oracle_value": ([U64, U64, U64], U64),
             "oracle_generate": ([U64, U64, U64, U64, U64, _P64], ctypes.c_int),
             "oracle_row_checksums": ([U64, U64, U64, U64, U64, _P64, _P64, U64, _P64], ctypes.c_int),
+            "oracle_output": ([U64, ctypes.c_int], U64),
+            "oracle_value_mode": ([U64, U64, U64, ctypes.c_int], U64),
+            "oracle_generate_mode": ([U64, U64, U64, U64, U64, ctypes.c_int, _P64], ctypes.c_int),
+            "oracle_row_checksums_mode": ([U64, U64, U64, U64, U64, ctypes.c_int, _P64, _P64, U64, _P64],
+                                          ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(l, name)
@@ -97,22 +102,31 @@ class OracleLib:
     def step_k(self, s: int, k: int) -> int:
         return int(self._l.oracle_step_k(s, k))
 
-    def value(self, g: int, seed: int, i: int) -> int:
+    def output(self, s: int, mode: int) -> int:
+        """Value emitted for state ``s`` in output mode ``mode`` (0: the state, 1: xorshift64*)."""
+        return int(self._l.oracle_output(s, mode))
+
+    def value(self, g: int, seed: int, i: int, output_mode: int = 0) -> int:
         """Output of stream ``g`` at iteration ``i``, computed on its own."""
+        if output_mode:
+            return int(self._l.oracle_value_mode(g, seed, i, output_mode))
         return int(self._l.oracle_value(g, seed, i))
 
     def generate(self, n_streams: int, seed: int, iterations: int, *, p0: int = 0,
-                 g0: int = 0) -> np.ndarray:
+                 g0: int = 0, output_mode: int = 0) -> np.ndarray:
         """Iterations ``p0 .. p0+T-1`` as a ``(T, N)`` uint64 array (iteration-major)."""
         out = np.empty((iterations, n_streams), dtype=np.uint64)
         if out.size:
-            rc = self._l.oracle_generate(n_streams, g0, seed, p0, iterations, _ptr(out))
+            if output_mode:
+                rc = self._l.oracle_generate_mode(n_streams, g0, seed, p0, iterations, output_mode, _ptr(out))
+            else:
+                rc = self._l.oracle_generate(n_streams, g0, seed, p0, iterations, _ptr(out))
             if rc != 0:
                 raise MemoryError("oracle_generate: allocation failed")
         return out
 
     def row_checksums(self, n_streams: int, seed: int, iterations: int, *, p0: int = 0,
-                      g0: int = 0, sample_every: int = 0):
+                      g0: int = 0, sample_every: int = 0, output_mode: int = 0):
         """Per-iteration (xor, wrapping sum) over all streams, plus every
         ``sample_every``-th row in full (``None`` when ``sample_every`` is 0)."""
         rx = np.zeros(iterations, dtype=np.uint64)
@@ -124,8 +138,12 @@ class OracleLib:
             samples = np.empty((n_s, n_streams), dtype=np.uint64)
             sp = _ptr(samples)
         if iterations:
-            rc = self._l.oracle_row_checksums(n_streams, g0, seed, p0, iterations, _ptr(rx),
-                                              _ptr(rs), sample_every, sp)
+            if output_mode:
+                rc = self._l.oracle_row_checksums_mode(n_streams, g0, seed, p0, iterations, output_mode,
+                                                       _ptr(rx), _ptr(rs), sample_every, sp)
+            else:
+                rc = self._l.oracle_row_checksums(n_streams, g0, seed, p0, iterations, _ptr(rx),
+                                                  _ptr(rs), sample_every, sp)
             if rc != 0:
                 raise MemoryError("oracle_row_checksums: allocation failed")
         return rx, rs, samples
@@ -148,6 +166,7 @@ def seed_key(seed): return lib().seed_key(seed)
 def initial_state(g, seed): return lib().initial_state(g, seed)
 def step(s): return lib().step(s)
 def step_k(s, k): return lib().step_k(s, k)
-def value(g, seed, i): return lib().value(g, seed, i)
+def output(s, mode): return lib().output(s, mode)
+def value(g, seed, i, output_mode=0): return lib().value(g, seed, i, output_mode)
 def generate(n_streams, seed, iterations, **kw): return lib().generate(n_streams, seed, iterations, **kw)
 def row_checksums(n_streams, seed, iterations, **kw): return lib().row_checksums(n_streams, seed, iterations, **kw)

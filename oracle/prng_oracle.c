@@ -30,6 +30,13 @@
  *   R4  the id is reduced to 32 bits before hashing (Listing S4 casts it).
  *   R8  row checksums are the XOR and the wrapping sum of one iteration's
  *       values over all streams.
+ *   R11 alternative output (the stronger generator the paper suggests
+ *       could replace plain xorshift): the xorshift64* scrambler of Vigna
+ *       ("An experimental exploration of Marsaglia's xorshift generators,
+ *       scrambled", ACM TOMS 42(4), 2016), i.e. the emitted value is the
+ *       state times the odd constant 2685821657736338717 modulo 2^64.  The
+ *       state sequence is the paper's, unchanged.  Output mode 0 is the
+ *       paper's (the state itself), mode 1 the scrambled value.
  *
  * Build: gcc -O2 -shared -fPIC prng_oracle.c -o liboracle.so
  */
@@ -122,6 +129,18 @@ uint64_t oracle_value(uint64_t g, uint64_t seed, uint64_t i)
     return oracle_step_k(oracle_initial_state(g, seed), i);
 }
 
+/* Reading R11: the value emitted for state s in output mode `mode`. */
+uint64_t oracle_output(uint64_t s, int mode)
+{
+    return mode ? s * 2685821657736338717ull : s;
+}
+
+/* Output value of stream g at iteration i in output mode `mode`. */
+uint64_t oracle_value_mode(uint64_t g, uint64_t seed, uint64_t i, int mode)
+{
+    return oracle_output(oracle_value(g, seed, i), mode);
+}
+
 /* ------------------------------------------------------------------ */
 /* Iterations p0 .. p0+T-1 of N streams, in the iteration-major layout */
 /* of Section 5 (one batch of N values per iteration, Eq. 1 gives the  */
@@ -129,8 +148,20 @@ uint64_t oracle_value(uint64_t g, uint64_t seed, uint64_t i)
 /* Streams are numbered from g0 (a shard of a larger generator).       */
 /* Returns 0, or -1 if the state array cannot be allocated.            */
 /* ------------------------------------------------------------------ */
+int oracle_generate_mode(uint64_t n_streams, uint64_t g0, uint64_t seed,
+                         uint64_t p0, uint64_t iterations, int mode,
+                         uint64_t *out);
+
 int oracle_generate(uint64_t n_streams, uint64_t g0, uint64_t seed,
                     uint64_t p0, uint64_t iterations, uint64_t *out)
+{
+    return oracle_generate_mode(n_streams, g0, seed, p0, iterations, 0, out);
+}
+
+/* The same in output mode `mode` (reading R11). */
+int oracle_generate_mode(uint64_t n_streams, uint64_t g0, uint64_t seed,
+                         uint64_t p0, uint64_t iterations, int mode,
+                         uint64_t *out)
 {
     if (n_streams == 0 || iterations == 0)
         return 0;
@@ -142,7 +173,7 @@ int oracle_generate(uint64_t n_streams, uint64_t g0, uint64_t seed,
     for (uint64_t i = 0; i < iterations; ++i) {
         uint64_t *row = out + i * n_streams;
         for (uint64_t g = 0; g < n_streams; ++g) {
-            row[g] = state[g];
+            row[g] = oracle_output(state[g], mode);
             state[g] = oracle_step(state[g]);
         }
     }
@@ -156,10 +187,25 @@ int oracle_generate(uint64_t n_streams, uint64_t g0, uint64_t seed,
 /* whose index (i - p0) is a multiple of sample_every are also copied  */
 /* out, one after another, into sample_rows (if it is not NULL).       */
 /* ------------------------------------------------------------------ */
+int oracle_row_checksums_mode(uint64_t n_streams, uint64_t g0, uint64_t seed,
+                              uint64_t p0, uint64_t iterations, int mode,
+                              uint64_t *row_xor, uint64_t *row_sum,
+                              uint64_t sample_every, uint64_t *sample_rows);
+
 int oracle_row_checksums(uint64_t n_streams, uint64_t g0, uint64_t seed,
                          uint64_t p0, uint64_t iterations,
                          uint64_t *row_xor, uint64_t *row_sum,
                          uint64_t sample_every, uint64_t *sample_rows)
+{
+    return oracle_row_checksums_mode(n_streams, g0, seed, p0, iterations, 0,
+                                     row_xor, row_sum, sample_every, sample_rows);
+}
+
+/* The same over the values of output mode `mode` (reading R11). */
+int oracle_row_checksums_mode(uint64_t n_streams, uint64_t g0, uint64_t seed,
+                              uint64_t p0, uint64_t iterations, int mode,
+                              uint64_t *row_xor, uint64_t *row_sum,
+                              uint64_t sample_every, uint64_t *sample_rows)
 {
     if (iterations == 0)
         return 0;
@@ -177,12 +223,12 @@ int oracle_row_checksums(uint64_t n_streams, uint64_t g0, uint64_t seed,
         int keep = sample_rows && sample_every && (i % sample_every == 0);
         uint64_t *dst = keep ? sample_rows + n_samples * n_streams : NULL;
         for (uint64_t g = 0; g < n_streams; ++g) {
-            uint64_t v = state[g];
+            uint64_t v = oracle_output(state[g], mode);
             x ^= v;
             s += v;
             if (dst)
                 dst[g] = v;
-            state[g] = oracle_step(v);
+            state[g] = oracle_step(state[g]);
         }
         row_xor[i] = x;
         row_sum[i] = s;

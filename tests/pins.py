@@ -16,7 +16,11 @@ What pins what:
 * the iteration-major layout and readings R2/R3 are pinned by brute force
   against matrix powers on tiny inputs;
 * the XOR row checksum by its closed form (linearity), the wrapping sum by
-  Python integers.
+  Python integers;
+* the alternative output mode (reading R11, xorshift64*: state times an odd
+  published constant) by undoing the multiplication with the constant's
+  modular inverse, which must give back the paper's pinned state sequence,
+  and its checksums by Python integers over the emitted values.
 """
 from __future__ import annotations
 
@@ -213,8 +217,44 @@ def check_row_checksums(o):
     assert (rx2 == rx[6:]).all() and (rs2 == rs[6:]).all()
 
 
+# xorshift64* multiplier (Vigna, "An experimental exploration of Marsaglia's
+# xorshift generators, scrambled", ACM TOMS 42(4), 2016).
+STAR_MULTIPLIER = 2685821657736338717
+STAR_INVERSE = pow(STAR_MULTIPLIER, -1, 1 << 64)
+
+
+def check_star_output(o):
+    """R11: every value of output mode 1, multiplied by the inverse of the
+    xorshift64* constant modulo 2^64, is the mode-0 value (the state), at the
+    same (iteration, stream); windows and single values agree with it."""
+    assert STAR_MULTIPLIER % 2 == 1 and (STAR_MULTIPLIER * STAR_INVERSE) % (1 << 64) == 1
+    for n_streams, seed, t, p0, g0 in [(1, 0, 3, 0, 0), (9, 12345, 6, 0, 0), (7, 99, 5, 4, 11)]:
+        plain = o.generate(n_streams, seed, t, p0=p0, g0=g0)
+        star = o.generate(n_streams, seed, t, p0=p0, g0=g0, output_mode=1)
+        for i in range(t):
+            for g in range(n_streams):
+                assert (int(star[i, g]) * STAR_INVERSE) % (1 << 64) == int(plain[i, g]), (seed, i, g)
+        c = 2 % n_streams
+        assert o.value(g0 + c, seed, p0 + t - 1, 1) == int(star[t - 1, c])
+    for s in EDGE64:
+        assert (o.output(s, 1) * STAR_INVERSE) % (1 << 64) == s and o.output(s, 0) == s
+
+
+def check_star_row_checksums(o):
+    n_streams, seed, t = 29, 7, 9
+    star = o.generate(n_streams, seed, t, output_mode=1)
+    rx, rs, samples = o.row_checksums(n_streams, seed, t, sample_every=3, output_mode=1)
+    for i in range(t):
+        x = 0
+        for v in star[i]:
+            x ^= int(v)
+        assert int(rx[i]) == x, i
+        assert int(rs[i]) == sum(int(v) for v in star[i]) % (1 << 64), i
+    assert (samples == star[::3]).all()
+
+
 ALL_CHECKS = [
     check_hash_low, check_hash_high, check_mix64, check_seed_key, check_initial_state,
     check_seed_alias_property, check_step_gf2, check_step_k, check_generate_layout,
-    check_generate_offsets, check_row_checksums,
+    check_generate_offsets, check_row_checksums, check_star_output, check_star_row_checksums,
 ]

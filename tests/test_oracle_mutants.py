@@ -26,8 +26,8 @@ MUTANTS = {
     "step_shift4": ("s ^ (s << 4)", "s ^ (s << 5)"),
     "word_order": ("((uint64_t)y << 32) | (uint64_t)x", "((uint64_t)x << 32) | (uint64_t)y"),
     "hash_input_not_id": ("oracle_hash_low(id32 ^ oracle_seed_key(seed))", "oracle_hash_low(id32 + oracle_seed_key(seed))"),
-    "emit_after_step": ("row[g] = state[g];\n            state[g] = oracle_step(state[g]);",
-                        "state[g] = oracle_step(state[g]);\n            row[g] = state[g];"),
+    "emit_after_step": ("row[g] = oracle_output(state[g], mode);\n            state[g] = oracle_step(state[g]);",
+                        "state[g] = oracle_step(state[g]);\n            row[g] = oracle_output(state[g], mode);"),
     "stream_major_layout": ("uint64_t *row = out + i * n_streams;", "uint64_t *row = out + i;"),
     "dropped_g0": ("state[g] = oracle_step_k(oracle_initial_state(g0 + g, seed), p0);\n    for (uint64_t i = 0; i < iterations; ++i) {\n        uint64_t *row",
                    "state[g] = oracle_step_k(oracle_initial_state(g, seed), p0);\n    for (uint64_t i = 0; i < iterations; ++i) {\n        uint64_t *row"),
@@ -36,6 +36,10 @@ MUTANTS = {
     "seed_fold": ("(uint32_t)(m & 0xffffffffu) ^ (uint32_t)(m >> 32)", "(uint32_t)(m & 0xffffffffu)"),
     "xor_checksum_or": ("x ^= v;", "x |= v;"),
     "sum_checksum_xor": ("s += v;", "s ^= v;"),
+    "star_constant": ("s * 2685821657736338717ull", "s * 2685821657736338719ull"),
+    "star_on_next_state": ("uint64_t v = oracle_output(state[g], mode);",
+                           "uint64_t v = oracle_output(oracle_step(state[g]), mode);"),
+    "star_always": ("return mode ? s * 2685821657736338717ull : s;", "return s * 2685821657736338717ull;"),
 }
 
 
