@@ -146,13 +146,13 @@ def parse_clock_samples(text: str):
             "samples": len(sms)}
 
 
-def cpu_oracle_sample(streams: int, seed: int, iterations: int):
+def cpu_oracle_sample(streams: int, seed: int, iterations: int, output_mode: int = 0):
     """Times the CPU oracle (single thread) on `iterations` rows of the workload."""
     sys.path.insert(0, ROOT)
     import oracle  # test infrastructure: the CPU baseline leg only
     oracle.build()
     t0 = time.perf_counter()
-    out = oracle.generate(streams, seed, iterations)
+    out = oracle.generate(streams, seed, iterations, output_mode=output_mode)
     dt = time.perf_counter() - t0
     return out.nbytes, dt
 
@@ -165,11 +165,11 @@ def _oracle_worker_init():
 
 def _oracle_worker(job):
     import oracle
-    n_sub, g0, seed, rows = job
-    return oracle.generate(n_sub, seed, rows, g0=g0).nbytes
+    n_sub, g0, seed, rows, mode = job
+    return oracle.generate(n_sub, seed, rows, g0=g0, output_mode=mode).nbytes
 
 
-def cpu_oracle_all_cores(streams: int, seed: int, iterations: int, reps: int = 3):
+def cpu_oracle_all_cores(streams: int, seed: int, iterations: int, reps: int = 3, output_mode: int = 0):
     """The same oracle, unchanged, run as one process per host core, each on a
     contiguous block of stream ids (the values of the whole workload, in
     column blocks).  Returns (bytes, median seconds of `reps` runs, processes)."""
@@ -179,11 +179,11 @@ def cpu_oracle_all_cores(streams: int, seed: int, iterations: int, reps: int = 3
     oracle.build()
     cores = os.cpu_count() or 1
     per = (streams + cores - 1) // cores
-    jobs = [(min(per, streams - g0), g0, seed, iterations) for g0 in range(0, streams, per)]
+    jobs = [(min(per, streams - g0), g0, seed, iterations, output_mode) for g0 in range(0, streams, per)]
     # spawn: this process already holds a CUDA context
     times = []
     with mp.get_context("spawn").Pool(len(jobs), initializer=_oracle_worker_init) as pool:
-        pool.map(_oracle_worker, [(1, 0, seed, 1)] * len(jobs), chunksize=1)
+        pool.map(_oracle_worker, [(1, 0, seed, 1, output_mode)] * len(jobs), chunksize=1)
         for _ in range(reps):
             t0 = time.perf_counter()
             nbytes = sum(pool.map(_oracle_worker, jobs, chunksize=1))
@@ -199,9 +199,9 @@ def run_reference(args, wl):
     rows = args.reference_rows
     times, nbytes = [], 0
     for _ in range(args.warmup):
-        cpu_oracle_sample(wl["streams"], wl["seed"], rows)
+        cpu_oracle_sample(wl["streams"], wl["seed"], rows, args.output_mode)
     for _ in range(args.steps):
-        nbytes, dt = cpu_oracle_sample(wl["streams"], wl["seed"], rows)
+        nbytes, dt = cpu_oracle_sample(wl["streams"], wl["seed"], rows, args.output_mode)
         times.append(dt)
     total = sum(times)
     gbs = nbytes * len(times) / total / 1e9
@@ -210,8 +210,9 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": wl["name"], "streams": wl["streams"], "iterations": wl["iterations"],
-                   "seed": wl["seed"], "parallelism": "none (host cores)"},
+        "config": {"workload": wl["name"] + _mode_label(args), "streams": wl["streams"],
+                   "iterations": wl["iterations"], "seed": wl["seed"], "output_mode": args.output_mode,
+                   "parallelism": "none (host cores)"},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{wl['streams']} streams x first {rows} iterations per step"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -247,7 +248,7 @@ def run_gpu(args, wl):
 
     n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
     nbytes = 8 * n * T
-    gen = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+    gen = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
                         init=False)
     stream = gen.stream
     out = torch.empty((T, n), dtype=torch.uint64, device="cuda")
@@ -327,11 +328,11 @@ def run_gpu(args, wl):
         # The paper's double buffer: two device buffers, copy engine reads.
         # Timed without the event profiler; one more profiled step gives the
         # kernel/read/overlap split.
-        gdb = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+        gdb = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
                             host_path=1, profiling=False, init=False)
         db_s, _ = host_leg(gdb, args.e2e_steps)
         gdb.close()
-        gdb = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+        gdb = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
                             host_path=1, init=False)
         _, prof = host_leg(gdb, 1)
         gdb.close()
@@ -342,7 +343,7 @@ def run_gpu(args, wl):
                               "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0],
                               "overlap_s": sum(prof["overlaps"].values())}}
         # The same double buffer with its reads done by a copy kernel.
-        gsm = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+        gsm = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
                             host_path=3, profiling=False, init=False)
         sm_s, _ = host_leg(gsm, args.e2e_steps)
         gsm.close()
@@ -354,7 +355,7 @@ def run_gpu(args, wl):
 
         # Host consumer (Section 5, "out" block): consumer threads fold every
         # row into its XOR and sum as it arrives through the staging slots.
-        gh = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+        gh = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
                            profiling=False, init=False)
 
         def step_host_checksum():
@@ -378,7 +379,7 @@ def run_gpu(args, wl):
 
         # The paper's program as measured there: every value to stdout, here
         # /dev/null, through the staging slots and one writer thread.
-        gf = rng.Generator(n, seed, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
+        gf = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
                            profiling=False, init=False)
         fd = os.open(os.devnull, os.O_WRONLY)
 
@@ -414,7 +415,8 @@ def run_gpu(args, wl):
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl["name"], "streams_per_gpu": n, "iterations": T, "seed": seed,
+        "config": {"workload": wl["name"] + _mode_label(args), "streams_per_gpu": n, "iterations": T,
+                   "seed": seed, "output_mode": args.output_mode,
                    "bytes_per_step_per_gpu": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
                    "l2": f"output {nbytes / GIB:g} GiB per step > 129 MB L2: no flush needed",
                    "parallelism": f"dp{ws} (disjoint stream-id blocks)"},
@@ -431,11 +433,11 @@ def run_gpu(args, wl):
     }
     if not args.skip_cpu_baseline and ws == 1:
         rows = args.cpu_rows or T
-        nb, dt = cpu_oracle_sample(n, seed, rows)
+        nb, dt = cpu_oracle_sample(n, seed, rows, args.output_mode)
         line["cpu_baseline"] = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} streams x first {rows} iterations ({nb / GIB:.1f} GiB), "
                                           f"single-threaded C oracle, {dt:.1f} s"}
-        nb_all, dt_all, procs = cpu_oracle_all_cores(n, seed, rows)
+        nb_all, dt_all, procs = cpu_oracle_all_cores(n, seed, rows, output_mode=args.output_mode)
         line["cpu_baseline"]["all_cores"] = {
             "value": nb_all / dt_all / 1e9, "unit": "GB/s", "cores": procs,
             "sample": f"the same {nb_all / GIB:.1f} GiB as {procs} processes of the oracle on contiguous "
@@ -481,6 +483,10 @@ def measure_host_link(torch, nbytes=GIB, reps=10):
             best = min(best, e0.elapsed_time(e1) * 1e-3)
     del dev, host
     return nbytes / best / 1e9
+
+
+def _mode_label(args) -> str:
+    return ", xorshift64* output (mode 1)" if args.output_mode == 1 else ""
 
 
 def _json_line(d):
@@ -579,7 +585,7 @@ def run_checksum(args, wl):
     import paper_1609_01257_gb300 as rng
 
     n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
-    g = rng.Generator(n, seed, init=False)
+    g = rng.Generator(n, seed, output_mode=args.output_mode, init=False)
     rx = torch.empty(T, dtype=torch.uint64, device="cuda")
     rs = torch.empty(T, dtype=torch.uint64, device="cuda")
     torch.cuda.synchronize()
@@ -614,12 +620,16 @@ def run_checksum(args, wl):
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0  # nominal maximum when nvidia-smi gave no sample
     peak = props.multi_processor_count * 64 * sm_mhz * 1e6 / 1e12
     achieved = vps * CHECKSUM_ALU_OPS_PER_VALUE / 1e12
-    line = {"workload": wl["name"] + " (generate-and-checksum mode)", "values_per_s": vps,
+    line = {"workload": wl["name"] + " (generate-and-checksum mode)" + _mode_label(args),
+            "values_per_s": vps,
             "equiv_GBps": 8 * vps / 1e9, "kernel_avg_ms": 1e3 * t / max(c, 1), "steps": args.steps,
             "sms": props.multi_processor_count,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (ALU-pipe lane ops)",
                          "frac": achieved / peak, "alu_ops_per_value": CHECKSUM_ALU_OPS_PER_VALUE,
-                         "peak_source": "SMs x 64 ALU lanes x median SM clock under load"},
+                         "peak_source": "SMs x 64 ALU lanes x median SM clock under load"}
+            if args.output_mode == 0 else None,
+            "roofline_note": None if args.output_mode == 0 else
+            "ALU ops per value captured for output mode 0 only; mode 1 adds a 64-bit multiply per value",
             "clocks": clk}
     if not args.skip_cpu_baseline:
         sys.path.insert(0, ROOT)
@@ -627,7 +637,7 @@ def run_checksum(args, wl):
         oracle.build()
         rows = min(T, args.cpu_rows or T)
         t0 = time.perf_counter()
-        oracle.row_checksums(n, seed, rows)
+        oracle.row_checksums(n, seed, rows, output_mode=args.output_mode)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": n * rows / dt, "unit": "values/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} streams x first {rows} iterations, row checksums, "
@@ -831,6 +841,8 @@ def main(argv=None):
                     help="skip: stream counts")
     ap.add_argument("--consumers", type=int, nargs="+", default=[1, 2, 4, 8, 16],
                     help="consumer: host consumer thread counts")
+    ap.add_argument("--output-mode", type=int, choices=[0, 1], default=0,
+                    help="streaming/checksum: 0 the paper's output, 1 xorshift64* scrambled values")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")

@@ -125,6 +125,19 @@ typedef struct rng_opts {
                                      Above 1, a sink is called concurrently
                                      from several threads, chunks in any
                                      order; rng_generate_fd always uses one */
+    uint32_t output_mode;         /* value emitted for each state: 0 (default)
+                                     the state itself, as in Section 5; 1 the
+                                     xorshift64* scrambled value (state times
+                                     0x2545F4914F6CDD1D modulo 2^64; Vigna,
+                                     ACM TOMS 42(4), 2016), the stronger
+                                     generator the paper says could replace
+                                     plain xorshift.  The state sequence,
+                                     rng_skip and the checkpoints are the same
+                                     in both modes; the checksums are over
+                                     the emitted values.  Mode 1 needs
+                                     block_threads 0 or 256 and
+                                     values_per_thread 0, 1, 2, 4, 8, 16, 24
+                                     or 32, and always uses streaming stores */
 } rng_opts;
 
 void rng_opts_default(rng_opts *opts);

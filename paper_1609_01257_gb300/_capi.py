@@ -46,6 +46,7 @@ class RngOpts(ctypes.Structure):
         ("grid_blocks", c_u32),
         ("host_path", c_u32),
         ("host_consumers", c_u32),
+        ("output_mode", c_u32),
     ]
 
 

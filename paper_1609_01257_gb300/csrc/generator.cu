@@ -183,9 +183,10 @@ int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh
   a.band_rows = 0;
   a.jump = nullptr;
   a.state_out = a.state;
+  a.out_mode = g->opts.output_mode;
   bool swap = false;
   if (!a.ring_rows && a.out && a.s_begin == 0 && a.s_end == g->n) {
-    const uint64_t br = rngi::choose_band_rows(g->n, a.rows, sh, g->device);
+    const uint64_t br = rngi::choose_band_rows(g->n, a.rows, sh, g->device, false, a.out_mode);
     if (br) {
       int rc = setup_bands(g, a, br, &swap, err);
       if (rc) return rc;
@@ -659,6 +660,15 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
   if (o.host_path > 3) return rngi::fail(err, RNG_EINVAL, "rng_create: host_path must be 0, 1, 2 or 3");
   if (o.host_consumers > 64) return rngi::fail(err, RNG_EINVAL, "rng_create: host_consumers must be at most 64");
+  if (o.output_mode > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: output_mode must be 0 or 1");
+  if (o.output_mode == 1) {
+    const uint32_t v = o.values_per_thread;
+    if ((o.block_threads && o.block_threads != rngi::kGenBlock) ||
+        !(v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 24 || v == 32))
+      return rngi::fail(err, RNG_EINVAL,
+                        "rng_create: output_mode 1 runs 256-thread blocks with 0, 1, 2, 4, 8, 16, 24 or 32 "
+                        "values per thread");
+  }
   if (o.store_width != 0 && o.store_width != 1 && o.store_width != 2 && o.store_width != 4)
     return rngi::fail(err, RNG_EINVAL, "rng_create: store_width must be 0, 1, 2 or 4");
   if (o.stream_offset > (uint64_t(1) << 32) - streams)
@@ -920,7 +930,8 @@ int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev
   sh.vpt = vpt;
   sh.block = rngi::kGenBlock;
   bool swap = false;
-  const uint64_t br = rngi::choose_band_rows(g->n, iterations, sh, g->device, true);
+  a.out_mode = g->opts.output_mode;
+  const uint64_t br = rngi::choose_band_rows(g->n, iterations, sh, g->device, true, a.out_mode);
   if (br) {
     rc = setup_bands(g, a, br, &swap, err);
     if (rc) return rc;

@@ -17,8 +17,12 @@ constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
 // Kernel entry points (kernels.cu); nullptr for shapes that are not compiled.
 // banded: the variant that splits rows into bands (few values per thread
 // only; store policy is always streaming there).
-const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded = false);
-const void *checksum_kernel_fn(uint32_t vpt, bool banded = false);
+// out: output mode (0: the state, 1: xorshift64*; mode 1 is compiled for
+// 256-thread blocks, streaming stores and 1, 2, 4, 8, 16, 24 or 32 values per
+// thread only).
+const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded = false,
+                           uint32_t out = 0);
+const void *checksum_kernel_fn(uint32_t vpt, bool banded = false, uint32_t out = 0);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *batch_work_kernel_fn(uint32_t vpt);
 const void *init_kernel_fn();
@@ -52,6 +56,7 @@ struct RowsLaunch {
   uint64_t band_rows;   // 0, or rows are split into bands of this many rows
   const uint64_t *jump; // bands: matrices M^(band * band_rows) for band = 0, 1, ..., 64 columns each
   uint64_t *state_out;  // where final states go (== state unless banded)
+  uint32_t out_mode;    // value emitted per state: 0 the state, 1 xorshift64* (selects the kernel)
 };
 
 struct LaunchShape {
@@ -141,7 +146,7 @@ int batch_blocks_per_sm(uint32_t vpt, uint32_t block);
 // streams, many rows: too few tiles to fill the GPU); 0 for no split.
 // `checksum`: for the generate-and-checksum kernel instead of the row kernel.
 uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device,
-                          bool checksum = false);
+                          bool checksum = false, uint32_t out = 0);
 // Most bands one banded launch is split into (one jump matrix each).
 constexpr uint32_t kMaxBands = 1024;
 // Host-side GF(2) tables for banded launches: writes `count` matrices

@@ -78,7 +78,8 @@ __device__ __forceinline__ uint64_t slot_offset(int j, int q) {
 // Emits `rows` rows of one tile, W values per store.  CHECK: some values of
 // the tile lie past the end of the stream range and must not be stored.
 // ring != 0: rows wrap around a ring of `ring` rows starting at `row`.
-template <int VPT, int W, int POLICY, bool CHECK, int BLOCK = kBlock>
+// OUT: output mode (the value emitted for each state, prng::emitted).
+template <int VPT, int W, int POLICY, bool CHECK, int BLOCK = kBlock, int OUT = 0>
 __device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, uint64_t pitch,
                                           uint64_t rows, uint64_t rel0, uint64_t span,
                                           uint64_t ring = 0) {
@@ -89,12 +90,15 @@ __device__ __forceinline__ void emit_rows(uint64_t (&st)[VPT], uint64_t *row, ui
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       const uint64_t rel = rel0 + slot_offset<W, BLOCK>(j, 0);
+      uint64_t v[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) v[q] = prng::emitted<OUT>(st[W * j + q]);
       if (!CHECK || rel + W <= span) {
-        store_vec<W, POLICY>(row + rel, &st[W * j]);
+        store_vec<W, POLICY>(row + rel, v);
       } else {
 #pragma unroll
         for (int q = 0; q < W; ++q)
-          if (rel + q < span) store_one<POLICY>(row + rel + q, st[W * j + q]);
+          if (rel + q < span) store_one<POLICY>(row + rel + q, v[q]);
       }
     }
 #pragma unroll
@@ -178,7 +182,7 @@ __device__ __forceinline__ void jump_states(uint64_t (&st)[VPT], const uint64_t 
 // (from the last band) go to state_out, which must not alias `state` (other
 // bands still read the starting states).  Blocks stride over units when the
 // grid is smaller than the unit count.
-template <int VPT, int W, int POLICY, int BLOCK, bool BANDED>
+template <int VPT, int W, int POLICY, int BLOCK, bool BANDED, int OUT = 0>
 __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
   const uint64_t span = a.s_end - a.s_begin;
   const uint64_t tile_vals = static_cast<uint64_t>(BLOCK) * VPT;
@@ -190,9 +194,9 @@ __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
       load_tile<VPT, W, BLOCK>(st, a, rel0, span);
       if (a.out) {
         if (rel0 + tile_vals <= span)
-          emit_rows<VPT, W, POLICY, false, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
+          emit_rows<VPT, W, POLICY, false, BLOCK, OUT>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
         else
-          emit_rows<VPT, W, POLICY, true, BLOCK>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
+          emit_rows<VPT, W, POLICY, true, BLOCK, OUT>(st, a.out, a.pitch, a.rows, rel0, span, a.ring_rows);
       } else {
         for (uint64_t r = 0; r < a.rows; ++r)
 #pragma unroll
@@ -215,9 +219,9 @@ __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
       const uint64_t rows = a.rows - r0 < band_rows ? a.rows - r0 : band_rows;
       uint64_t *out = a.out + r0 * a.pitch;
       if (rel0 + tile_vals <= span)
-        emit_rows<VPT, W, POLICY, false, BLOCK>(st, out, a.pitch, rows, rel0, span);
+        emit_rows<VPT, W, POLICY, false, BLOCK, OUT>(st, out, a.pitch, rows, rel0, span);
       else
-        emit_rows<VPT, W, POLICY, true, BLOCK>(st, out, a.pitch, rows, rel0, span);
+        emit_rows<VPT, W, POLICY, true, BLOCK, OUT>(st, out, a.pitch, rows, rel0, span);
       if (a.write_state && band == n_bands - 1) store_tile_state<VPT, W, BLOCK>(st, a.state_out, a, rel0, span);
     }
   }
@@ -292,7 +296,7 @@ __device__ __forceinline__ void warp_xor_sum(uint64_t &x, uint64_t &s) {
 // Banded (BANDED = true): work units are (tile, band of band_rows rows), each
 // unit jumping its states ahead to its band over GF(2) as in the row kernel;
 // final states go to state_out (from the last band).
-template <int VPT, bool BANDED>
+template <int VPT, bool BANDED, int OUT = 0>
 __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
                                                        unsigned long long *row_xor,
                                                        unsigned long long *row_sum) {
@@ -320,8 +324,9 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
       uint64_t x = 0, s = 0;
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
-        x ^= st[v];
-        s += st[v];
+        const uint64_t e = prng::emitted<OUT>(st[v]);
+        x ^= e;
+        s += e;
         st[v] = prng::xorshift_update(st[v]);
       }
       warp_xor_sum(x, s);
@@ -553,6 +558,32 @@ const void *select_rows_banded(uint32_t vpt, int width) {
   }
 }
 
+// Output mode 1 (xorshift64*): 256-thread blocks and streaming stores only;
+// 8-byte stores from six values per thread up, as in the default shapes.
+template <int VPT, bool BANDED>
+const void *rows_star_dispatch(int width) {
+  if constexpr (VPT % 4 == 0 && VPT < 6) {
+    if (width >= 4) return reinterpret_cast<const void *>(&rows_kernel<VPT, 4, kPolicyStreaming, kBlock, BANDED, 1>);
+  }
+  if constexpr (VPT % 2 == 0 && VPT < 6) {
+    if (width >= 2) return reinterpret_cast<const void *>(&rows_kernel<VPT, 2, kPolicyStreaming, kBlock, BANDED, 1>);
+  }
+  return reinterpret_cast<const void *>(&rows_kernel<VPT, 1, kPolicyStreaming, kBlock, BANDED, 1>);
+}
+
+const void *select_rows_star(uint32_t vpt, int width, bool banded) {
+  switch (vpt) {
+    case 1: return banded ? rows_star_dispatch<1, true>(width) : rows_star_dispatch<1, false>(width);
+    case 2: return banded ? rows_star_dispatch<2, true>(width) : rows_star_dispatch<2, false>(width);
+    case 4: return banded ? rows_star_dispatch<4, true>(width) : rows_star_dispatch<4, false>(width);
+    case 8: return banded ? rows_star_dispatch<8, true>(width) : rows_star_dispatch<8, false>(width);
+    case 16: return banded ? rows_star_dispatch<16, true>(width) : rows_star_dispatch<16, false>(width);
+    case 24: return banded ? nullptr : rows_star_dispatch<24, false>(width);
+    case 32: return banded ? nullptr : rows_star_dispatch<32, false>(width);
+    default: return nullptr;
+  }
+}
+
 const void *select_rows(uint32_t vpt, int width, int policy, uint32_t block = kBlock) {
   if (block == 512) return rows_fn_wide<512>(vpt);
   if (block == 1024) return rows_fn_wide<1024>(vpt);
@@ -569,22 +600,24 @@ const void *select_rows(uint32_t vpt, int width, int policy, uint32_t block = kB
   }
 }
 
-template <bool BANDED>
+template <bool BANDED, int OUT>
 const void *select_checksum_t(uint32_t vpt) {
   switch (vpt) {
-    case 1: return reinterpret_cast<const void *>(&checksum_kernel<1, BANDED>);
-    case 2: return reinterpret_cast<const void *>(&checksum_kernel<2, BANDED>);
-    case 4: return reinterpret_cast<const void *>(&checksum_kernel<4, BANDED>);
-    case 8: return reinterpret_cast<const void *>(&checksum_kernel<8, BANDED>);
-    case 16: return reinterpret_cast<const void *>(&checksum_kernel<16, BANDED>);
-    case 32: return reinterpret_cast<const void *>(&checksum_kernel<32, BANDED>);
-    case 64: return reinterpret_cast<const void *>(&checksum_kernel<64, BANDED>);
+    case 1: return reinterpret_cast<const void *>(&checksum_kernel<1, BANDED, OUT>);
+    case 2: return reinterpret_cast<const void *>(&checksum_kernel<2, BANDED, OUT>);
+    case 4: return reinterpret_cast<const void *>(&checksum_kernel<4, BANDED, OUT>);
+    case 8: return reinterpret_cast<const void *>(&checksum_kernel<8, BANDED, OUT>);
+    case 16: return reinterpret_cast<const void *>(&checksum_kernel<16, BANDED, OUT>);
+    case 32: return reinterpret_cast<const void *>(&checksum_kernel<32, BANDED, OUT>);
+    case 64: return reinterpret_cast<const void *>(&checksum_kernel<64, BANDED, OUT>);
     default: return nullptr;
   }
 }
 
-const void *select_checksum(uint32_t vpt, bool banded) {
-  return banded ? select_checksum_t<true>(vpt) : select_checksum_t<false>(vpt);
+const void *select_checksum(uint32_t vpt, bool banded, uint32_t out) {
+  if (out == 1) return banded ? select_checksum_t<true, 1>(vpt) : select_checksum_t<false, 1>(vpt);
+  if (out != 0) return nullptr;
+  return banded ? select_checksum_t<true, 0>(vpt) : select_checksum_t<false, 0>(vpt);
 }
 
 const void *select_batch(uint32_t vpt) {
@@ -606,11 +639,13 @@ const void *select_batch(uint32_t vpt) {
 
 // Kernel entry points for the host-side launch code (launch.cpp); nullptr
 // when a shape is not compiled.
-const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded) {
+const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded, uint32_t out) {
+  if (out == 1) return block == kBlock ? select_rows_star(vpt, width, banded) : nullptr;
+  if (out != 0) return nullptr;
   if (banded) return block == kBlock ? select_rows_banded(vpt, width) : nullptr;
   return select_rows(vpt, width, policy, block);
 }
-const void *checksum_kernel_fn(uint32_t vpt, bool banded) { return select_checksum(vpt, banded); }
+const void *checksum_kernel_fn(uint32_t vpt, bool banded, uint32_t out) { return select_checksum(vpt, banded, out); }
 const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }
 const void *batch_work_kernel_fn(uint32_t vpt) { return select_batch_work(vpt); }
 const void *init_kernel_fn() { return reinterpret_cast<const void *>(&init_kernel); }

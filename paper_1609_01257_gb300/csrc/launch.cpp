@@ -99,7 +99,7 @@ cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_po
       break;
     }
   if (width > static_cast<int>(sh.width)) width = static_cast<int>(sh.width);
-  const void *fn = rows_kernel_fn(sh.vpt, width, store_policy, sh.block, a.band_rows != 0);
+  const void *fn = rows_kernel_fn(sh.vpt, width, store_policy, sh.block, a.band_rows != 0, a.out_mode);
   if (!fn) return cudaErrorInvalidValue;
   RowsLaunch args = a;
   void *params[] = {&args};
@@ -215,12 +215,13 @@ void jump_table(uint64_t band_rows, uint32_t count, uint64_t *cols) {
 // resident block slots empty, up to about four units per slot, so that the
 // last wave of units is a small part of the launch.
 // Bands hold at least 128 rows, which amortises each unit's jump.
-uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device, bool checksum) {
+uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh, int device, bool checksum,
+                          uint32_t out) {
   const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
   const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
   const uint64_t min_band = 128;
-  const void *fn = checksum ? checksum_kernel_fn(sh.vpt, true)
-                            : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true);
+  const void *fn = checksum ? checksum_kernel_fn(sh.vpt, true, out)
+                            : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true, out);
   if (!fn || rows < 2 * min_band) return 0;  // no banded variant of this shape, or too few rows
   uint64_t target;
   if (checksum) {
@@ -277,7 +278,7 @@ cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor
   cudaGetDevice(&dev);
   const int sms = device_sm_count(dev);
   if (a.band_rows && (!a.jump || (a.write_state && a.state_out == a.state))) return cudaErrorInvalidValue;
-  const void *fn = checksum_kernel_fn(vpt, a.band_rows != 0);
+  const void *fn = checksum_kernel_fn(vpt, a.band_rows != 0, a.out_mode);
   if (!fn) return cudaErrorInvalidValue;
   const uint64_t tiles = (span + uint64_t(kGenBlock) * vpt - 1) / (uint64_t(kGenBlock) * vpt);
   const uint64_t units = a.band_rows ? tiles * ((a.rows + a.band_rows - 1) / a.band_rows) : tiles;

@@ -71,4 +71,17 @@ PRNG_HD uint64_t xorshift_update(uint64_t s) {
   return s;
 }
 
+// Alternative output mode: the xorshift64* scrambler (Vigna, "An experimental
+// exploration of Marsaglia's xorshift generators, scrambled", ACM TOMS 42(4),
+// 2016) -- the value emitted for a state is the state times this odd
+// constant modulo 2^64; the state sequence itself is unchanged.
+constexpr uint64_t kStarMultiplier = 0x2545F4914F6CDD1Dull;
+
+// Value emitted for state s in output mode OUT (0: the state, as in the
+// paper; 1: xorshift64*).
+template <int OUT>
+PRNG_HD uint64_t emitted(uint64_t s) {
+  return OUT ? s * kStarMultiplier : s;
+}
+
 }  // namespace prng

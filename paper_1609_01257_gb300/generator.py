@@ -36,7 +36,8 @@ class Generator:
                  device_buffer_bytes: int = 32 << 20, host_slots: int = 0, host_consumers: int = 0,
                  profiling: bool = True, compute_stream=None, device: Optional[int] = None,
                  store_policy: int = 1, host_wait_ms: int = 0, store_width: int = 0,
-                 block_threads: int = 0, grid_blocks: int = 0, host_path: int = 0, init: bool = True):
+                 block_threads: int = 0, grid_blocks: int = 0, host_path: int = 0, output_mode: int = 0,
+                 init: bool = True):
         lib = C.load()
         o = C.RngOpts()
         lib.rng_opts_default(ctypes.byref(o))
@@ -61,6 +62,7 @@ class Generator:
         o.block_threads = block_threads
         o.grid_blocks = grid_blocks
         o.host_path = host_path
+        o.output_mode = output_mode
         self._lib = lib
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

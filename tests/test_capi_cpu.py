@@ -80,6 +80,7 @@ def test_option_structs_match_the_header(L):
     o = C.RngOpts()
     L.rng_opts_default(ctypes.byref(o))
     assert (o.host_slots, o.host_consumers, o.host_path, o.store_policy, o.fuse_init) == (0, 0, 0, 1, 1)
+    assert o.output_mode == 0
     assert o.device_buffer_bytes == 32 << 20 and o.profiling == 1 and o.device == -1
 
 
