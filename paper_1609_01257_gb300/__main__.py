@@ -14,9 +14,12 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0, help="run seed (0: the paper's generator)")
     ap.add_argument("--buffer-bytes", type=int, default=32 << 20, help="size of each device buffer")
     ap.add_argument("--profile", action="store_true", help="print the profiling summary to stderr")
+    ap.add_argument("--output-mode", type=int, choices=[0, 1], default=0,
+                    help="0: the paper's values (the states); 1: xorshift64* scrambled values")
     args = ap.parse_args(argv)
     from . import Generator
-    g = Generator(args.n, args.seed, device_buffer_bytes=args.buffer_bytes, host_path=1)
+    g = Generator(args.n, args.seed, device_buffer_bytes=args.buffer_bytes, host_path=1,
+                  output_mode=args.output_mode)
     sys.stdout.flush()
     g.generate_fd(args.i, sys.stdout.fileno())
     if args.profile:

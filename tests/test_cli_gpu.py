@@ -39,6 +39,15 @@ def test_cli_stdout_matches_oracle():
     assert b"Aggregate times by event" in r.stderr
 
 
+def test_cli_output_mode_1():
+    n, T = 777, 4
+    r = subprocess.run([sys.executable, "-m", "paper_1609_01257_gb300", str(n), str(T), "--seed", "5",
+                        "--output-mode", "1"], cwd=ROOT, capture_output=True, timeout=300)
+    assert r.returncode == 0, r.stderr.decode()
+    got = np.frombuffer(r.stdout, dtype=np.uint64).reshape(T, n)
+    assert np.array_equal(got, oracle.generate(n, 5, T, output_mode=1))
+
+
 def test_c_example_program_matches_oracle():
     # The paper's program as a plain C client of the library (built by build()).
     from paper_1609_01257_gb300 import builder
