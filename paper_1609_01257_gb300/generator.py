@@ -27,8 +27,13 @@ class Generator:
 
     ``generate(T)`` returns the next ``T`` iterations as a ``(T, streams)``
     uint64 CUDA tensor (iteration-major, value ``[i, g]``); iteration 0 is the
-    init value.  ``generate_to_host`` streams the same values into host
-    memory through the double-buffered copy path.
+    init value.  ``generate_to_host`` writes the same values into host memory:
+    by default the kernel stores them there directly; ``host_path=1`` uses the
+    paper's double buffer with copy-engine reads, ``host_path=3`` the double
+    buffer with copy-kernel reads, ``host_path=2`` insists on direct stores.
+    The keyword options mirror ``rng_opts`` in ``include/rng.h``
+    (``output_mode=1``: xorshift64* values of the same states;
+    ``host_consumers``: host threads draining the staging slots).
     """
 
     def __init__(self, streams: int, seed: int = 0, *, values_per_thread: int = 0,
