@@ -45,10 +45,11 @@ WORKLOADS = {
                   name="plain method: 2^16 streams x 100 iterations, seed 0"),
 }
 
-# ALU-pipe lane operations per value of checksum_kernel<16>, from its ncu
-# capture: 85.6 % ALU-pipe utilisation x 64 lanes x 152 SMs x 1.85 GHz x
-# 184.3 us over 2^22 x 64 values.
-CHECKSUM_ALU_OPS_PER_VALUE = 10.6
+# ALU-pipe lane operations per value of checksum_kernel<16> in output modes
+# 0 and 1, from their ncu captures: ALU-pipe utilisation (85.5 %, 74.9 %) x 64
+# lanes x 152 SMs x 1.85 GHz x duration (184.2 us, 209.7 us) over 2^22 x 64
+# values.
+CHECKSUM_ALU_OPS_PER_VALUE = {0: 10.6, 1: 10.5}
 NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e, nominal
 METRIC = "GB/s of uint64 PRNG output (device and host-streamed) vs roofline; p50/p99 req latency"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rows_kernel_traffic.md")
@@ -619,17 +620,15 @@ def run_checksum(args, wl):
     # duration / values).
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0  # nominal maximum when nvidia-smi gave no sample
     peak = props.multi_processor_count * 64 * sm_mhz * 1e6 / 1e12
-    achieved = vps * CHECKSUM_ALU_OPS_PER_VALUE / 1e12
+    ops = CHECKSUM_ALU_OPS_PER_VALUE[args.output_mode]
+    achieved = vps * ops / 1e12
     line = {"workload": wl["name"] + " (generate-and-checksum mode)" + _mode_label(args),
             "values_per_s": vps,
             "equiv_GBps": 8 * vps / 1e9, "kernel_avg_ms": 1e3 * t / max(c, 1), "steps": args.steps,
             "sms": props.multi_processor_count,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (ALU-pipe lane ops)",
-                         "frac": achieved / peak, "alu_ops_per_value": CHECKSUM_ALU_OPS_PER_VALUE,
-                         "peak_source": "SMs x 64 ALU lanes x median SM clock under load"}
-            if args.output_mode == 0 else None,
-            "roofline_note": None if args.output_mode == 0 else
-            "ALU ops per value captured for output mode 0 only; mode 1 adds a 64-bit multiply per value",
+                         "frac": achieved / peak, "alu_ops_per_value": ops,
+                         "peak_source": "SMs x 64 ALU lanes x median SM clock under load"},
             "clocks": clk}
     if not args.skip_cpu_baseline:
         sys.path.insert(0, ROOT)
