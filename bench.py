@@ -92,35 +92,78 @@ def _traffic_per_launch(workload: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every `interval_ms` from
+    before the warm-up until after the timed region; each line is stamped
+    with the host time it arrived, so the samples that fall inside the timed
+    region can be told apart."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
+        self.lines = []
+        self.reader = None
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
+        """Starts sampling and waits (up to wait_s) for the first sample."""
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                bufsize=1)
         except OSError:
             self.proc = None
+            return
 
-    def stop(self):
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.time(), line))
+
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        end = time.time() + wait_s
+        while not self.lines and time.time() < end:
+            time.sleep(0.01)
+
+    def stop(self, t0: float | None = None, t1: float | None = None):
+        """Median clock etc. of the samples stamped within [t0, t1] (host
+        time around the timed region); if the region was shorter than the
+        sampling interval, of every sample taken since start()."""
         if not self.proc:
             return None
-        time.sleep(0.25)
+        time.sleep(2 * self.interval_ms / 1e3)
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        return parse_clock_samples(out)
+            self.proc.wait()
+        if self.reader:
+            self.reader.join(timeout=5)
+        res = clocks_in_window(list(self.lines), t0, t1)
+        if res is not None:
+            res["interval_ms"] = self.interval_ms
+        return res
+
+
+def clocks_in_window(lines, t0, t1):
+    """parse_clock_samples over the (host time, line) samples stamped within
+    [t0, t1]; over all of them when none is (a timed region shorter than the
+    sampling interval)."""
+    res, window = None, "timed region"
+    if t0 is not None and t1 is not None:
+        res = parse_clock_samples("".join(l for ts, l in lines if t0 <= ts <= t1))
+    if res is None:
+        res = parse_clock_samples("".join(l for _, l in lines))
+        window = "warm-up and timed region (the timed region is shorter than the sampling interval)"
+    if res is not None:
+        res["window"] = window
+    return res
 
 
 def parse_clock_samples(text: str):
@@ -260,23 +303,25 @@ def run_gpu(args, wl):
         gen.generate_to(T, out.data_ptr())
 
     # ---- device-resident leg ------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step_device()
     gen.sync()
     barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     gen.profile_reset()
     launches0 = rng.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_start = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         step_device()
     e1.record(stream)
     e1.synchronize()
+    t_end = time.time()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_start, t_end)
     launches = rng.launch_count() - launches0
     dev_s = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
     k_count, k_total = gen.profile_stat("RNG_KERNEL")
@@ -595,21 +640,23 @@ def run_checksum(args, wl):
         g.init()
         g.generate_checksum(T, rx, rs)
 
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for _ in range(args.warmup):
         step()
     g.sync()
     g.profile_reset()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s = g.stream
+    t_start = time.time()
     e0.record(s)
     for _ in range(args.steps):
         step()
     e1.record(s)
     e1.synchronize()
+    t_end = time.time()
     secs = e0.elapsed_time(e1) * 1e-3
-    clk = clocks.stop()
+    clk = clocks.stop(t_start, t_end)
     c, t = g.profile_stat("CHECKSUM_KERNEL")
     g.close()
     props = torch.cuda.get_device_properties(0)

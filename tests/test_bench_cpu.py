@@ -16,6 +16,18 @@ garbage line
     assert bench.parse_clock_samples("") is None
 
 
+def test_clock_samples_inside_the_timed_region():
+    warm = "0, 1500, 2070, 300.0, 0x1, Not Active, Not Active, Not Active, Not Active\n"
+    busy = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Active\n"
+    lines = [(1.0, warm), (2.0, busy), (2.1, busy), (3.0, warm)]
+    c = bench.clocks_in_window(lines, 1.9, 2.2)
+    assert c["sm_mhz"] == 2070.0 and c["samples"] == 2 and c["window"] == "timed region"
+    assert c["reasons"] == ["sw_power_cap"]
+    c = bench.clocks_in_window(lines, 2.5, 2.6)  # no sample inside: all of them
+    assert c["samples"] == 4 and c["window"].startswith("warm-up")
+    assert bench.clocks_in_window([], 0, 1) is None
+
+
 def test_traffic_lookup_tracks_kernel_sources(tmp_path, monkeypatch):
     f = tmp_path / "t.md"
     f.write_text(f"kernel_source_sha256_16: {bench._kernel_source_hash()}\n"
