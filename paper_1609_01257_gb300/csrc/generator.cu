@@ -245,20 +245,36 @@ struct Chunk {
 
 // Splits `T` iterations of `n` streams into chunks that fit one device buffer:
 // whole rows when a row fits (as many rows as fit), else one row split into
-// column slabs.
-std::vector<Chunk> plan_chunks(uint64_t n, uint64_t T, size_t buf_bytes) {
-  std::vector<Chunk> v;
-  const uint64_t cap_vals = buf_bytes / 8;
-  if (n <= cap_vals) {
-    const uint64_t R = cap_vals / n;
-    for (uint64_t r = 0; r < T; r += R) v.push_back({r, (T - r) < R ? (T - r) : R, 0, n});
-  } else {
-    const uint64_t C = cap_vals & ~uint64_t(1);
-    for (uint64_t r = 0; r < T; ++r)
-      for (uint64_t s = 0; s < n; s += C) v.push_back({r, 1, s, (n - s) < C ? (n - s) : C});
+// column slabs.  Chunks are computed from their index, so a call of any
+// length needs no list of them.
+struct ChunkPlan {
+  uint64_t n = 0, T = 0;
+  uint64_t rows_per = 0;  // rows per chunk (whole-row chunks), else 0
+  uint64_t slab = 0;      // streams per column slab (one-row chunks)
+  uint64_t per_row = 1;   // column slabs per row
+  uint64_t count = 0;     // chunks
+
+  ChunkPlan(uint64_t n_, uint64_t T_, size_t buf_bytes) : n(n_), T(T_) {
+    const uint64_t cap_vals = buf_bytes / 8;
+    if (n <= cap_vals) {
+      rows_per = cap_vals / n;
+      count = (T + rows_per - 1) / rows_per;
+    } else {
+      slab = cap_vals & ~uint64_t(1);
+      per_row = (n + slab - 1) / slab;
+      count = T * per_row;  // <= T * n, which the size check bounds
+    }
   }
-  return v;
-}
+
+  Chunk at(uint64_t c) const {
+    if (rows_per) {
+      const uint64_t r = c * rows_per;
+      return {r, (T - r) < rows_per ? (T - r) : rows_per, 0, n};
+    }
+    const uint64_t s = (c % per_row) * slab;
+    return {c / per_row, 1, s, (n - s) < slab ? (n - s) : slab};
+  }
+};
 
 int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_err **err) {
   rngi::RowsLaunch a{};
@@ -429,16 +445,16 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
     cudaGetLastError();
   }
   const bool staged = !pinned;
-  const std::vector<Chunk> chunks = plan_chunks(g->n, T, g->buf_bytes);
+  const ChunkPlan chunks(g->n, T, g->buf_bytes);
   // No more consumers than chunks; two slots beyond the consumers keep the
   // copy engine busy while every consumer holds one.
-  tgt.consumers = static_cast<unsigned>(std::max<size_t>(1, std::min<size_t>(tgt.consumers, chunks.size())));
+  tgt.consumers = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(tgt.consumers, chunks.count)));
   size_t slots = 0;
   if (staged) slots = g->opts.host_slots ? std::max<uint32_t>(2, g->opts.host_slots) : tgt.consumers + 2;
   int rc = ensure_buffers(g, slots, err);
   if (rc) return rc;
   if (staged) slots = g->h_slots.size();
-  reserve_events(g, 2 * chunks.size());  // one kernel and one read per chunk
+  reserve_events(g, 2 * std::min<uint64_t>(chunks.count, kMaxOps));  // one kernel and one read per chunk
   const bool hash_first_rows = !g->materialized;
   const uint64_t first_it = g->pos;
   g->initialized = false;  // re-armed only if the whole run succeeds
@@ -467,8 +483,8 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
 
   int status = RNG_OK;
   std::string status_msg;
-  for (size_t c = 0; c < chunks.size() && status == RNG_OK; ++c) {
-    const Chunk &ck = chunks[c];
+  for (uint64_t c = 0; c < chunks.count && status == RNG_OK; ++c) {
+    const Chunk ck = chunks.at(c);
     const int b = static_cast<int>(c & 1);
     size_t slot = 0;
     if (staged) {
@@ -534,7 +550,7 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
   cudaError_t st2 = cudaStreamSynchronize(g->compute);
   rng_host_stats &hs = g->host_stats;
   hs = rng_host_stats{};
-  hs.chunks = chunks.size();
+  hs.chunks = chunks.count;
   hs.consumers = staged ? static_cast<uint32_t>(cons.th.size()) : 0;
   hs.slots = staged ? static_cast<uint32_t>(slots) : 0;
   hs.wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - call0).count();
