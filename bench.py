@@ -293,7 +293,7 @@ def run_gpu(args, wl):
     n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
     nbytes = 8 * n * T
     gen = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
-                        init=False)
+                        values_per_thread=args.values_per_thread, block_threads=args.block_threads, init=False)
     stream = gen.stream
     out = torch.empty((T, n), dtype=torch.uint64, device="cuda")
     torch.cuda.synchronize()
@@ -303,27 +303,31 @@ def run_gpu(args, wl):
         gen.generate_to(T, out.data_ptr())
 
     # ---- device-resident leg ------------------------------------------------
+    if L2Flush.needed(torch, nbytes):
+        flush = L2Flush(torch)
+        l2_note = flush.label()
+    else:
+        flush = None
+        l2_note = (f"output {nbytes / GIB:g} GiB per step > 4 x {L2Flush.l2_size(torch) / 1e6:.0f} MB L2: "
+                   "no flush needed")
     clocks = ClockSampler(local)
     clocks.start()
     for _ in range(args.warmup):
+        if flush:
+            flush(stream)
         step_device()
     gen.sync()
     barrier()
     gen.profile_reset()
     launches0 = rng.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     t_start = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step_device()
-    e1.record(stream)
-    e1.synchronize()
+    dev_s = timed_steps(torch, stream, step_device, args.steps, flush)
     t_end = time.time()
     barrier()
     clk = clocks.stop(t_start, t_end)
     launches = rng.launch_count() - launches0
-    dev_s = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+    del flush
+    dev_s = max_over_ranks(dev_s)
     k_count, k_total = gen.profile_stat("RNG_KERNEL")
     k_avg = max_over_ranks(k_total / max(k_count, 1))
     value = nbytes * ws * args.steps / dev_s / 1e9
@@ -464,7 +468,7 @@ def run_gpu(args, wl):
         "config": {"workload": wl["name"] + _mode_label(args), "streams_per_gpu": n, "iterations": T,
                    "seed": seed, "output_mode": args.output_mode,
                    "bytes_per_step_per_gpu": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
-                   "l2": f"output {nbytes / GIB:g} GiB per step > 129 MB L2: no flush needed",
+                   "l2": l2_note,
                    "parallelism": f"dp{ws} (disjoint stream-id blocks)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -529,6 +533,62 @@ def measure_host_link(torch, nbytes=GIB, reps=10):
             best = min(best, e0.elapsed_time(e1) * 1e-3)
     del dev, host
     return nbytes / best / 1e9
+
+
+class L2Flush:
+    """Evicts the output of the previous step from L2: writes a buffer of
+    four times the L2 size on the given stream.  Used, outside the timed
+    events, when one step writes less than that (the plain 52 MB workload;
+    small jump-ahead states), so that each timed step starts from a cold L2."""
+
+    def __init__(self, torch):
+        self.l2_bytes = self.l2_size(torch)
+        self.buf = torch.empty(4 * self.l2_bytes // 4, dtype=torch.int32, device="cuda")
+        self.torch = torch
+        self.n = 0
+
+    @staticmethod
+    def l2_size(torch) -> int:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return int(getattr(props, "L2_cache_size", 0)) or 129 * 10**6
+
+    @staticmethod
+    def needed(torch, step_bytes: int) -> bool:
+        return step_bytes < 4 * L2Flush.l2_size(torch)
+
+    def __call__(self, stream):
+        self.n += 1
+        with self.torch.cuda.stream(stream):
+            self.buf.fill_(self.n)
+
+    def label(self) -> str:
+        return (f"L2 ({self.l2_bytes / 1e6:.0f} MB) flushed before every timed step by writing "
+                f"{4 * self.l2_bytes / 1e6:.0f} MB outside the step's events; time = sum of the steps' events")
+
+
+def timed_steps(torch, stream, step, steps: int, flush=None) -> float:
+    """Seconds for `steps` calls of `step`, from CUDA events on `stream`.
+    Without `flush`: one event pair around all steps.  With it: the flush
+    runs before each step, outside that step's own event pair, and the
+    result is the sum of the per-step times."""
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+    pairs = []
+    for _ in range(steps):
+        flush(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        pairs.append((a, b))
+    pairs[-1][1].synchronize()
+    return sum(a.elapsed_time(b) for a, b in pairs) * 1e-3
 
 
 def _mode_label(args) -> str:
@@ -709,20 +769,19 @@ def run_skip(args):
         for _ in range(args.warmup):
             g.skip(k)
         g.sync()
+        # States smaller than L2 would stay there between calls: flush it
+        # before each timed call (outside the call's events).
+        flush = L2Flush(torch) if L2Flush.needed(torch, 8 * n) else None
         g.profile_reset()
-        s = g.stream
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(args.steps):
-            g.skip(k)
-        e1.record(s)
-        e1.synchronize()
+        call_s = timed_steps(torch, g.stream, lambda: g.skip(k), args.steps, flush)
         c, kt = g.profile_stat("SKIP_KERNEL")
         g.close()
         kern = kt / max(c, 1)
         gbs = 16 * n / kern / 1e9
-        points.append({"streams": n, "call_ms": e0.elapsed_time(e1) / args.steps, "kernel_ms": 1e3 * kern,
-                       "states_per_s": n / kern, "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]})
+        points.append({"streams": n, "call_ms": 1e3 * call_s / args.steps, "kernel_ms": 1e3 * kern,
+                       "states_per_s": n / kern, "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"],
+                       "l2": flush.label() if flush else "state > 4 x L2: no flush needed"})
+        del flush
     _json_line({"workload": "jump-ahead by 2^40 + 12345 iterations", "unit": "GB/s of state read + written",
                 "peak": peaks["hbm_gbs"], "peak_source": f"{src}: hbm_gbs (copy) from MEASURED_PEAKS.json",
                 "points": points, "steps": args.steps})
@@ -895,6 +954,10 @@ def main(argv=None):
     ap.add_argument("--cpu-rows", type=int, default=0,
                     help="iterations in the CPU-baseline sample (0 = the whole workload)")
     ap.add_argument("--reference-rows", type=int, default=128, help="iterations per reference step")
+    ap.add_argument("--values-per-thread", type=int, default=0,
+                    help="streaming/plain device leg: streams per thread of the row kernel (0 = the library's choice)")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="streaming/plain device leg: threads per block of the row kernel (0 = 256)")
     ap.add_argument("--iterations", type=int, default=0,
                     help="override the workload's iteration count (profiling captures of a smaller case)")
     args = ap.parse_args(argv)
