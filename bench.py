@@ -293,7 +293,9 @@ def run_gpu(args, wl):
     n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
     nbytes = 8 * n * T
     gen = rng.Generator(n, seed, output_mode=args.output_mode, stream_offset=rank * n, device_buffer_bytes=wl["device_buffer_bytes"],
-                        values_per_thread=args.values_per_thread, block_threads=args.block_threads, init=False)
+                        values_per_thread=args.values_per_thread, block_threads=args.block_threads,
+                        store_width=args.store_width, grid_blocks=args.grid_blocks, store_policy=args.store_policy,
+                        init=False)
     stream = gen.stream
     out = torch.empty((T, n), dtype=torch.uint64, device="cuda")
     torch.cuda.synchronize()
@@ -468,6 +470,8 @@ def run_gpu(args, wl):
         "config": {"workload": wl["name"] + _mode_label(args), "streams_per_gpu": n, "iterations": T,
                    "seed": seed, "output_mode": args.output_mode,
                    "bytes_per_step_per_gpu": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
+                   "stores": {"widest_values": args.store_width or "per shape",
+                              "policy": "streaming (st.global.cs)" if args.store_policy else "default"},
                    "l2": l2_note,
                    "parallelism": f"dp{ws} (disjoint stream-id blocks)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -958,6 +962,13 @@ def main(argv=None):
                     help="streaming/plain device leg: streams per thread of the row kernel (0 = the library's choice)")
     ap.add_argument("--block-threads", type=int, default=0,
                     help="streaming/plain device leg: threads per block of the row kernel (0 = 256)")
+    ap.add_argument("--store-width", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="streaming/plain device leg: widest store in values (0 = per shape)")
+    ap.add_argument("--grid-blocks", type=int, default=0,
+                    help="streaming/plain device leg: row-kernel grid (0 = one block per tile; fewer: "
+                         "persistent blocks striding over the tiles)")
+    ap.add_argument("--store-policy", type=int, default=1, choices=[0, 1],
+                    help="streaming/plain device leg: 1 = streaming stores (st.global.cs), 0 = default stores")
     ap.add_argument("--iterations", type=int, default=0,
                     help="override the workload's iteration count (profiling captures of a smaller case)")
     args = ap.parse_args(argv)
