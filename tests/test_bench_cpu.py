@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py: clock-sample parsing, the traffic lookup
-(reported only while the kernel sources match the capture), peaks."""
+(reported only while the kernel sources match the capture), peaks, and the
+step timing with an L2 flush outside each step's events."""
 import os
 
 import bench
@@ -37,6 +38,39 @@ def test_traffic_lookup_tracks_kernel_sources(tmp_path, monkeypatch):
     assert bench._traffic_per_launch("plain") is None
     f.write_text("kernel_source_sha256_16: 0000000000000000\ntraffic_bytes_per_launch[streaming]: 3.5e+10\n")
     assert bench._traffic_per_launch("streaming") is None
+
+
+class _FakeEvent:
+    """Stand-in for torch.cuda.Event: the clock advances by one unit per
+    record, so elapsed times count the records between two events."""
+    clock = 0.0
+
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream):
+        _FakeEvent.clock += 1.0
+        self.t = _FakeEvent.clock
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+def test_timed_steps_flush_outside_the_step_events():
+    import types
+    fake = types.SimpleNamespace(cuda=types.SimpleNamespace(Event=_FakeEvent))
+    log = []
+    # One event pair around all steps: 2 records 1 unit apart (ms -> s).
+    assert bench.timed_steps(fake, None, lambda: log.append("step"), 4) == 1e-3
+    log.clear()
+    # With a flush: each step has its own pair, the flush runs before it and
+    # outside it, and the result sums the steps (3 x 1 unit).
+    t = bench.timed_steps(fake, None, lambda: log.append("step"), 3, flush=lambda s: log.append("flush"))
+    assert t == 3e-3
+    assert log == ["flush", "step"] * 3
 
 
 def test_peaks_file_is_read():
