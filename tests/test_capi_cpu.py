@@ -172,3 +172,32 @@ def test_shard_range_partitions(total, world):
         first, count = lib.shard_range(total, r, world)
         seen.extend(range(first, first + count))
     assert seen == list(range(total))
+
+
+def test_noalloc_rejects_bad_batches_before_any_cuda_call(L):
+    # Every check of the allocation-free entry point runs on the host before
+    # it looks at a device, so each bad batch fails the same way without a GPU.
+    U64 = ctypes.c_uint64
+
+    def call(streams, iterations, outs, count=None):
+        k = len(streams) if count is None else count
+        n = max(len(streams), 1)
+        err = ctypes.POINTER(C.RngErr)()
+        rc = L.rng_batch_generate_noalloc(k, (U64 * n)(*streams), (U64 * n)(*iterations), (U64 * n)(*([1] * n)),
+                                          (ctypes.c_void_p * n)(*outs), None, ctypes.byref(err))
+        msg = err.contents.msg if err else b""
+        L.rng_err_clear(ctypes.byref(err))
+        return rc, msg
+
+    fake = 1 << 20  # a pointer value that is only range- and alignment-checked, never used
+    assert call([], [], [], count=0)[0] == C.RNG_EINVAL
+    assert call([16] * 4097, [1] * 4097, [fake] * 4097)[1].find(b"at most 4096") > 0
+    assert call([0], [1], [fake])[0] == C.RNG_EINVAL
+    assert call([(1 << 32) + 1], [1], [fake])[0] == C.RNG_EINVAL
+    assert call([16], [0], [fake])[0] == C.RNG_EINVAL
+    assert call([16], [1], [0])[0] == C.RNG_EINVAL                       # NULL output
+    assert b"aligned" in call([16], [1], [fake + 4])[1]
+    assert b"overflows" in call([1 << 32], [1 << 40], [fake])[1]
+    rc, msg = call([1 << 32], [1], [fake])                                # 2^21 units of 2048 streams
+    assert rc == C.RNG_EINVAL and b"work units" in msg
+    assert L.rng_batch_generate_noalloc(1, None, None, None, None, None, None) == C.RNG_EINVAL
