@@ -201,3 +201,48 @@ def test_noalloc_rejects_bad_batches_before_any_cuda_call(L):
     rc, msg = call([1 << 32], [1], [fake])                                # 2^21 units of 2048 streams
     assert rc == C.RNG_EINVAL and b"work units" in msg
     assert L.rng_batch_generate_noalloc(1, None, None, None, None, None, None) == C.RNG_EINVAL
+
+
+def test_batch_and_server_options_are_checked_on_the_host(L):
+    # Option and size checks of the batched and served constructors run
+    # before they look at a device: each bad value fails without a GPU and
+    # creates no object.
+    U64 = ctypes.c_uint64
+    before = L.rng_live_objects()
+    h = ctypes.c_void_p()
+    fake = 1 << 20
+
+    def batch(opts=None, streams=16, iterations=1, out=fake):
+        err = ctypes.POINTER(C.RngErr)()
+        rc = L.rng_batch_create(1, (U64 * 1)(streams), (U64 * 1)(iterations), (U64 * 1)(1),
+                                (ctypes.c_void_p * 1)(out), ctypes.byref(opts) if opts else None,
+                                ctypes.byref(h), ctypes.byref(err))
+        msg = err.contents.msg if err else b""
+        L.rng_err_clear(ctypes.byref(err))
+        return rc, msg
+
+    o = C.RngBatchOpts()
+    L.rng_batch_opts_default(ctypes.byref(o))
+    for field, bad in [("values_per_thread", 3), ("mode", 3), ("block_threads", 128), ("struct_size", 8)]:
+        b = C.RngBatchOpts()
+        ctypes.memmove(ctypes.byref(b), ctypes.byref(o), ctypes.sizeof(o))
+        setattr(b, field, bad)
+        assert batch(b)[0] == C.RNG_EINVAL, field
+    assert batch(streams=0)[0] == C.RNG_EINVAL
+    assert batch(streams=(1 << 32) + 1)[0] == C.RNG_EINVAL
+    assert batch(iterations=0)[0] == C.RNG_EINVAL
+    assert b"aligned" in batch(out=fake + 4)[1]
+    assert b"overflows" in batch(streams=1 << 32, iterations=1 << 40)[1]
+    assert L.rng_batch_create(1, None, None, None, None, None, None, None) == C.RNG_EINVAL
+
+    s = C.RngServerOpts()
+    L.rng_server_opts_default(ctypes.byref(s))
+    for field, bad in [("values_per_thread", 3), ("mode", 0), ("mode", 3), ("max_active", 0),
+                       ("max_steps_in_flight", 0), ("step_bytes", 0), ("max_units_per_step", 0),
+                       ("hbm_budget_bytes", 255), ("struct_size", 8)]:
+        b = C.RngServerOpts()
+        ctypes.memmove(ctypes.byref(b), ctypes.byref(s), ctypes.sizeof(s))
+        setattr(b, field, bad)
+        assert L.rng_server_create(ctypes.byref(b), ctypes.byref(h), None) == C.RNG_EINVAL, field
+    assert L.rng_server_create(None, None, None) == C.RNG_EINVAL
+    assert not h and L.rng_live_objects() == before
