@@ -246,3 +246,32 @@ def test_batch_and_server_options_are_checked_on_the_host(L):
         assert L.rng_server_create(ctypes.byref(b), ctypes.byref(h), None) == C.RNG_EINVAL, field
     assert L.rng_server_create(None, None, None) == C.RNG_EINVAL
     assert not h and L.rng_live_objects() == before
+
+
+@pytest.mark.parametrize("field,bad", [
+    ("values_per_thread", 9), ("block_threads", 384), ("device_buffer_bytes", 24), ("device_buffer_bytes", 8),
+    ("store_policy", 2), ("host_path", 4), ("host_consumers", 65), ("output_mode", 2), ("store_width", 3),
+    ("stream_offset", (1 << 32) - 15),
+])
+def test_generator_options_are_checked_on_the_host(L, field, bad):
+    # rng_create checks every option before it looks at a device.
+    o = C.RngOpts()
+    L.rng_opts_default(ctypes.byref(o))
+    setattr(o, field, bad)
+    h = ctypes.c_void_p()
+    err = ctypes.POINTER(C.RngErr)()
+    before = L.rng_live_objects()
+    assert L.rng_create(16, 1, ctypes.byref(o), ctypes.byref(h), ctypes.byref(err)) == C.RNG_EINVAL
+    assert err and err.contents.code == C.RNG_EINVAL and b"rng_create" in err.contents.msg
+    L.rng_err_clear(ctypes.byref(err))
+    assert not h and L.rng_live_objects() == before
+
+
+def test_alternative_output_mode_shapes_are_checked_on_the_host(L):
+    o = C.RngOpts()
+    L.rng_opts_default(ctypes.byref(o))
+    o.output_mode = 1
+    h = ctypes.c_void_p()
+    for vpt, block in [(6, 0), (12, 0), (8, 128)]:
+        o.values_per_thread, o.block_threads = vpt, block
+        assert L.rng_create(4096, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL, (vpt, block)
