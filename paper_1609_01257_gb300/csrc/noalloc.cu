@@ -1,15 +1,16 @@
 // Batched generation for callers that cannot allocate device memory.
 //
-// rng_batch_create (batch.cu) allocates its work tables, a work counter and a
-// CUDA graph with cudaMalloc.  Some callers cannot do that: code running while
-// a CUDA stream is being captured into a graph by someone else, code inside a
-// framework whose memory pool owns the whole device and forbids other
-// allocations, or latency-bound callers that must not pay for an allocation
-// (and the device-wide synchronisation a cudaFree implies) per call.  This
-// entry point runs the same work-list kernel as the batched form, but its
-// scratch -- the work counter and the two tables -- lives in one fixed-size
-// array in device global memory declared at file scope below.  Every GPU that
-// loads the library holds this array until the process exits.
+// rng_batch_create (batch.cu) allocates its work records, a work counter and
+// a CUDA graph with cudaMalloc.  Some callers cannot do that: code inside a
+// framework whose memory pool owns the whole device and forbids allocations
+// beside it, or latency-bound callers that must not pay for an allocation
+// (and the device-wide synchronisation a cudaFree implies) on every call.
+// This entry point produces the batched form's output with the served form's
+// work-list kernel (worklist_kernel: an instance table, a unit table and a
+// work counter), whose scratch -- the counter and the two tables, 48 bytes
+// per instance and 16 per unit -- lives in one fixed-size array in device
+// global memory declared at file scope below.  Every GPU that loads the
+// library holds this array until the process exits.
 //
 // Host code cannot use the array's name as a device address (it names a
 // host-side stand-in), so the address is looked up with
