@@ -8,13 +8,22 @@ per step).  One step = rng_init + rng_generate over the whole workload.
   value), the output written into a 32 GiB device buffer (larger than L2, so
   no flush is needed between steps), timed with CUDA events on the
   generator's compute stream.
-* ``e2e``: the same step through the C ABI with a host output buffer
-  (page-locked, 32 GiB): values are generated into two 32 MiB device
-  buffers and copied to the host on a copy stream while the next buffer is
-  generated; the timed region includes every device-to-host byte.
+* ``e2e``: the same step through the C ABI with a host output buffer (32 GiB
+  of page-locked memory from rng_host_alloc, backed by transparent huge
+  pages): by default the kernel stores straight into it over the host link;
+  ``e2e.double_buffer`` times the paper's double buffer (two 32 MiB device
+  buffers, copy-engine reads on a copy stream while the next buffer is
+  generated).  Every timed region includes every device-to-host byte.
 * ``roofline``: the row kernel's average launch time from the library's own
   CUDA events (recorded on the stream it launches on) over the timed region.
 * ``cpu_baseline``: the CPU oracle timed on a bounded sample on rank 0.
+* ``plain``, ``batched``, ``checksum``, ``sweep``, ``served`` (one GPU): the
+  other workloads -- the plain method (2^16 x 100), the batched form (512
+  instances, 8 GiB, one CUDA-graph launch) against the plain form, the
+  generate-and-checksum mode against its integer-ALU roofline, a compact
+  roofline sweep over stream counts, and the served form (Poisson 2000
+  req/s for ``--duration`` seconds, p50/p99 latency) -- each with its own
+  config and the clocks sampled during its own timed region.
 
 ``--impl reference`` times the CPU oracle instead (the method's plain
 definition, single-threaded) on a bounded sample of the same workload.
@@ -130,6 +139,18 @@ class ClockSampler:
         while not self.lines and time.time() < end:
             time.sleep(0.01)
 
+    def window(self, t0: float, t1: float):
+        """Median clock etc. of the samples stamped within [t0, t1], while
+        sampling goes on (the samples nearest to a region shorter than the
+        sampling interval)."""
+        if not self.proc:
+            return None
+        time.sleep(2 * self.interval_ms / 1e3)  # let the sample after t1 arrive
+        res = clocks_in_window(list(self.lines), t0, t1, margin_s=2 * self.interval_ms / 1e3)
+        if res is not None:
+            res["interval_ms"] = self.interval_ms
+        return res
+
     def stop(self, t0: float | None = None, t1: float | None = None):
         """Median clock etc. of the samples stamped within [t0, t1] (host
         time around the timed region); if the region was shorter than the
@@ -151,13 +172,17 @@ class ClockSampler:
         return res
 
 
-def clocks_in_window(lines, t0, t1):
+def clocks_in_window(lines, t0, t1, margin_s: float | None = None):
     """parse_clock_samples over the (host time, line) samples stamped within
-    [t0, t1]; over all of them when none is (a timed region shorter than the
-    sampling interval)."""
+    [t0, t1].  When none is (a timed region shorter than the sampling
+    interval): over those within `margin_s` of it if given, else over all."""
     res, window = None, "timed region"
     if t0 is not None and t1 is not None:
         res = parse_clock_samples("".join(l for ts, l in lines if t0 <= ts <= t1))
+        if res is None and margin_s is not None:
+            res = parse_clock_samples("".join(l for ts, l in lines if t0 - margin_s <= ts <= t1 + margin_s))
+            window = (f"samples within {1e3 * margin_s:.0f} ms of the timed region "
+                      "(shorter than the sampling interval)")
     if res is None:
         res = parse_clock_samples("".join(l for _, l in lines))
         window = "warm-up and timed region (the timed region is shorter than the sampling interval)"
@@ -326,7 +351,7 @@ def run_gpu(args, wl):
     dev_s = timed_steps(torch, stream, step_device, args.steps, flush)
     t_end = time.time()
     barrier()
-    clk = clocks.stop(t_start, t_end)
+    clk = clocks.window(t_start, t_end)
     launches = rng.launch_count() - launches0
     del flush
     dev_s = max_over_ranks(dev_s)
@@ -349,7 +374,12 @@ def run_gpu(args, wl):
         # buffers together stay well inside host memory.  Same bytes over
         # the link either way.
         rows = T if ws == 1 else max(1, min(T, (2 * GIB) // (8 * n)))
-        host = torch.empty((rows, n), dtype=torch.uint64).pin_memory()
+        # Page-locked destination from the library's allocator (transparent
+        # huge pages): into 64 KiB pages the copies over the host link stall
+        # intermittently (`--workload host-dest`).
+        host = rng.host_empty((rows, n))
+        dest = {"allocator": "rng_host_alloc (anonymous memory, transparent huge pages, cudaHostRegister)",
+                "bytes": host.nbytes, "huge_page_share": huge_page_share(host)}
 
         def host_leg(g, steps):
             def step_host():
@@ -376,7 +406,7 @@ def run_gpu(args, wl):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes,
                "steps": args.e2e_steps, "ms_per_step": 1e3 * host_s / args.e2e_steps,
                "path": "direct stores into page-locked host memory",
-               "iterations_per_call": rows}
+               "iterations_per_call": rows, "destination": dest}
         # The paper's double buffer: two device buffers, copy engine reads.
         # Timed without the event profiler; one more profiled step gives the
         # kernel/read/overlap split.
@@ -454,12 +484,23 @@ def run_gpu(args, wl):
                                  "ms_per_step": 1e3 * fd_s / args.e2e_steps, "last_step": fd_stats}
 
     gen.close()
+    peaks, src = _peaks()
+    # The other workloads (the plain method, batched and served forms,
+    # generate-and-checksum mode, the roofline sweep), each timed in its own
+    # window with its own clock summary; one GPU only.
+    extra = {}
+    if ws == 1 and not args.skip_configs:
+        extra["plain"] = plain_leg(args, clocks, write_ceiling, peaks["hbm_gbs"])
+        extra["batched"] = batched_leg(args, clocks, write_ceiling)
+        extra["checksum"] = checksum_leg(args, WORKLOADS["streaming"], clocks)
+        extra["sweep"] = sweep_leg(args, clocks)
+        extra["served"] = served_leg(args, clocks)
+    clocks.stop()
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return 0
 
-    peaks, src = _peaks()
     achieved = nbytes / k_avg / 1e9
     traffic = _traffic_per_launch(args.workload)
     line = {
@@ -485,6 +526,7 @@ def run_gpu(args, wl):
         "e2e": e2e,
         "clocks": clk,
     }
+    line.update(extra)
     if not args.skip_cpu_baseline and ws == 1:
         rows = args.cpu_rows or T
         nb, dt = cpu_oracle_sample(n, seed, rows, args.output_mode)
@@ -500,6 +542,25 @@ def run_gpu(args, wl):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def huge_page_share(arr) -> float | None:
+    """Share of the memory mapping holding `arr` that transparent huge pages
+    back (AnonHugePages / Size in /proc/self/smaps); None when unreadable."""
+    addr = arr.ctypes.data
+    try:
+        with open("/proc/self/smaps") as f:
+            inside, size = False, None
+            for line in f:
+                head = line.split(None, 1)[0]
+                if "-" in head and not head.endswith(":"):
+                    a, b = (int(x, 16) for x in head.split("-"))
+                    inside, size = a <= addr < b, b - a
+                elif inside and head == "AnonHugePages:":
+                    return int(line.split()[1]) * 1024 / size
+    except (OSError, ValueError):
+        pass
+    return None
 
 
 def measure_write_ceiling(torch, nbytes=2 * GIB, reps=10):
@@ -603,10 +664,16 @@ def _json_line(d):
     print(json.dumps(d), flush=True)
 
 
-def run_batched(args):
+BATCHED_NAME = ("batched: 512 instances, streams log-uniform [2^8, 2^20], iterations log-uniform [1, 4096] "
+                "capped at {cap:g} GiB, seeds splitmix64 from 7, one CUDA-graph launch")
+SERVED_NAME = ("served: Poisson 2000 req/s for {dur:g} s, streams log-uniform [2^10, 2^22], iterations "
+               "log-uniform [1, 512], seeds splitmix64 from 99, 64 GiB HBM budget, device outputs")
+
+
+def batched_leg(args, clocks=None, write_ceiling=None):
     """Batched form: 512 independent instances (log-uniform sizes, 8 GiB total)
     in one CUDA-graph launch, against the plain form (one generator and one
-    launch per instance) on the same GPU."""
+    launch per instance) on the same GPU.  Output 8 GiB per step (> L2)."""
     import torch
     sys.path.insert(0, ROOT)
     import paper_1609_01257_gb300 as rng
@@ -622,12 +689,15 @@ def run_batched(args):
         b.run()
     b.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
     e0.record(s)
     for _ in range(args.steps):
         b.run()
     e1.record(s)
     e1.synchronize()
+    t1 = time.time()
     batched_s = e0.elapsed_time(e1) * 1e-3 / args.steps
+    clk = clocks.window(t0, t1) if clocks else None
     # Plain form: one generator per instance, launched one after another.
     plain_stream = torch.cuda.Stream()
     gens = [rng.Generator(i.streams, i.seed, compute_stream=plain_stream, profiling=False, init=False)
@@ -650,16 +720,32 @@ def run_batched(args):
     for g in gens:
         g.close()
     b.close()
-    _json_line({"workload": "batched: 512 instances, streams log-uniform [2^8, 2^20], iterations log-uniform "
-                            f"[1, 4096] capped at {args.batch_cap_gib:g} GiB, seeds splitmix64 from 7",
-                "bytes_per_step": total, "batched_GBps": total / batched_s / 1e9, "batched_ms": batched_s * 1e3,
-                "plain_GBps": total / plain_s / 1e9, "plain_ms": plain_s * 1e3, "tuned": cfg,
-                "steps": args.steps, "warmup": args.warmup})
+    d = {"config": {"workload": BATCHED_NAME.format(cap=args.batch_cap_gib), "instances": len(inst),
+                    "bytes_per_step": total, "tuned": cfg,
+                    "l2": f"output {total / GIB:.1f} GiB per step > L2: no flush needed"},
+         "value": total / batched_s / 1e9, "unit": "GB/s", "ms_per_step": batched_s * 1e3,
+         "plain_form_GBps": total / plain_s / 1e9, "plain_form_ms": plain_s * 1e3,
+         "batched_over_plain_form": plain_s / batched_s, "steps": args.steps, "warmup": args.warmup}
+    if write_ceiling:
+        d["frac_write_ceiling"] = d["value"] / write_ceiling
+    if clocks:
+        d["clocks"] = clk
+    return d
+
+
+def run_batched(args):
+    d = batched_leg(args)
+    _json_line({"workload": d["config"]["workload"], "bytes_per_step": d["config"]["bytes_per_step"],
+                "batched_GBps": d["value"], "batched_ms": d["ms_per_step"], "plain_GBps": d["plain_form_GBps"],
+                "plain_ms": d["plain_form_ms"], "tuned": d["config"]["tuned"], "steps": args.steps,
+                "warmup": args.warmup})
     return 0
 
 
-def run_served(args):
-    """Served form: Poisson arrivals (2000/s), continuous batching, 64 GiB budget."""
+def served_leg(args, clocks=None):
+    """Served form: Poisson arrivals (2000/s) for `args.duration` seconds,
+    continuous batching, 64 GiB budget; latency from submission to the
+    output being complete on the device."""
     sys.path.insert(0, ROOT)
     import paper_1609_01257_gb300 as rng
     import workloads
@@ -671,25 +757,36 @@ def run_served(args):
                     mode=args.server_mode) as srv:
         warm = workloads.served_requests(duration_s=0.5, seed_start=5, arrival_start=6, size_start=7)
         rng.run_load(srv, warm)
+        t0 = time.time()
         res = rng.run_load(srv, reqs)
+        t1 = time.time()
         st = srv.stats()
-    _json_line({"workload": f"served: Poisson 2000 req/s for {args.duration:g} s, streams log-uniform [2^10, 2^22], "
-                            "iterations log-uniform [1, 512], seeds splitmix64 from 99, 64 GiB budget",
-                "requests": len(reqs), "p50_ms": res.percentile(50) * 1e3, "p99_ms": res.percentile(99) * 1e3,
-                "max_ms": max(res.latencies_s.values()) * 1e3,
-                "aggregate_GBps": res.bytes / res.wall_s / 1e9, "offered_GBps": offered / args.duration / 1e9,
-                "wall_s": res.wall_s, "worst_submit_lag_ms": res.submit_lag_s * 1e3,
-                "steps": st["steps"], "peak_active": st["peak_active"],
-                "server": {"step_bytes": args.step_bytes, "steps_in_flight": args.steps_in_flight,
-                           "values_per_thread": args.server_vpt, "mode": args.server_mode},
-                "peak_bytes_in_use": st["peak_bytes_in_use"]})
+    d = {"config": {"workload": SERVED_NAME.format(dur=args.duration), "window_s": args.duration,
+                    "server": {"step_bytes": args.step_bytes, "steps_in_flight": args.steps_in_flight,
+                               "values_per_thread": args.server_vpt, "mode": args.server_mode}},
+         "requests": len(reqs), "p50_ms": res.percentile(50) * 1e3, "p99_ms": res.percentile(99) * 1e3,
+         "max_ms": max(res.latencies_s.values()) * 1e3,
+         "aggregate_GBps": res.bytes / res.wall_s / 1e9, "offered_GBps": offered / args.duration / 1e9,
+         "wall_s": res.wall_s, "worst_submit_lag_ms": res.submit_lag_s * 1e3,
+         "steps": st["steps"], "peak_active": st["peak_active"], "peak_bytes_in_use": st["peak_bytes_in_use"]}
+    if clocks:
+        d["clocks"] = clocks.window(t0, t1)
+    return d
+
+
+def run_served(args):
+    d = served_leg(args)
+    line = {"workload": d["config"]["workload"]}
+    line.update({k: v for k, v in d.items() if k != "config"})
+    line["server"] = d["config"]["server"]
+    _json_line(line)
     return 0
 
 
-def run_checksum(args, wl):
+def checksum_leg(args, wl, clocks=None):
     """Generate-and-checksum mode on the streaming workload: every value is
     produced and folded into its row's XOR and wrapping sum; nothing is
-    stored.  Bound by integer issue, not memory."""
+    stored.  Bound by integer issue on the ALU pipe, not memory."""
     import torch
     sys.path.insert(0, ROOT)
     import paper_1609_01257_gb300 as rng
@@ -704,8 +801,10 @@ def run_checksum(args, wl):
         g.init()
         g.generate_checksum(T, rx, rs)
 
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    own = clocks is None
+    if own:
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
     for _ in range(args.warmup):
         step()
     g.sync()
@@ -720,7 +819,7 @@ def run_checksum(args, wl):
     e1.synchronize()
     t_end = time.time()
     secs = e0.elapsed_time(e1) * 1e-3
-    clk = clocks.stop(t_start, t_end)
+    clk = clocks.stop(t_start, t_end) if own else clocks.window(t_start, t_end)
     c, t = g.profile_stat("CHECKSUM_KERNEL")
     g.close()
     props = torch.cuda.get_device_properties(0)
@@ -733,18 +832,26 @@ def run_checksum(args, wl):
     peak = props.multi_processor_count * 64 * sm_mhz * 1e6 / 1e12
     ops = CHECKSUM_ALU_OPS_PER_VALUE[args.output_mode]
     achieved = vps * ops / 1e12
-    line = {"workload": wl["name"] + " (generate-and-checksum mode)" + _mode_label(args),
+    return {"config": {"workload": wl["name"] + " (generate-and-checksum mode)" + _mode_label(args),
+                       "streams": n, "iterations": T, "seed": seed},
             "values_per_s": vps,
             "equiv_GBps": 8 * vps / 1e9, "kernel_avg_ms": 1e3 * t / max(c, 1), "steps": args.steps,
             "sms": props.multi_processor_count,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (ALU-pipe lane ops)",
                          "frac": achieved / peak, "alu_ops_per_value": ops,
-                         "peak_source": "SMs x 64 ALU lanes x median SM clock under load"},
+                         "peak_source": "SMs x 64 ALU-pipe lanes x median SM clock during the timed region"},
             "clocks": clk}
+
+
+def run_checksum(args, wl):
+    line = checksum_leg(args, wl)
+    line = dict(line, workload=line["config"]["workload"])
+    del line["config"]
     if not args.skip_cpu_baseline:
         sys.path.insert(0, ROOT)
         import oracle  # test infrastructure: the CPU baseline leg only
         oracle.build()
+        n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
         rows = min(T, args.cpu_rows or T)
         t0 = time.perf_counter()
         oracle.row_checksums(n, seed, rows, output_mode=args.output_mode)
@@ -754,6 +861,104 @@ def run_checksum(args, wl):
                                           f"single-threaded C oracle, {dt:.1f} s"}
     _json_line(line)
     return 0
+
+
+def plain_leg(args, clocks=None, write_ceiling=None, peak=None):
+    """The plain method (2^16 streams x 100 iterations, seed 0, 52 MB,
+    device-resident): L2 flushed before every timed step, outside its events."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    wl = WORKLOADS["plain"]
+    n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
+    g = rng.Generator(n, seed, init=False)
+    out = torch.empty((T, n), dtype=torch.uint64, device="cuda")
+    flush = L2Flush(torch)
+    torch.cuda.synchronize()
+
+    def step():
+        g.init()
+        g.generate_to(T, out.data_ptr())
+
+    steps = max(args.steps, 100)
+    for _ in range(args.warmup):
+        flush(g.stream)
+        step()
+    g.sync()
+    g.profile_reset()
+    t0 = time.time()
+    secs = timed_steps(torch, g.stream, step, steps, flush)
+    t1 = time.time()
+    c, kt = g.profile_stat("RNG_KERNEL")
+    vpt, block, grid = g.launch_config()
+    g.close()
+    k_avg = kt / max(c, 1)
+    nbytes = 8 * n * T
+    d = {"config": {"workload": wl["name"], "streams": n, "iterations": T, "seed": seed,
+                    "bytes_per_step": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
+                    "l2": flush.label()},
+         "value": nbytes * steps / secs / 1e9, "unit": "GB/s", "us_per_step": 1e6 * secs / steps,
+         "kernel_us": 1e6 * k_avg, "kernel_GBps": nbytes / k_avg / 1e9, "steps": steps, "warmup": args.warmup}
+    if write_ceiling:
+        d["kernel_frac_write_ceiling"] = d["kernel_GBps"] / write_ceiling
+    if peak:
+        d["kernel_frac_hbm_peak"] = d["kernel_GBps"] / peak
+    if clocks:
+        d["clocks"] = clocks.window(t0, t1)
+    del flush
+    return d
+
+
+def sweep_leg(args, clocks=None):
+    """Compact roofline sweep for the default line: at each stream count 2^16
+    .. 2^28 (powers of 4), the library's default shape in full-write mode
+    (4 GiB ring per launch, four launches) and in generate-and-checksum
+    mode (16 GiB worth of values)."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    ring = torch.empty(GIB // 2, dtype=torch.uint64, device="cuda")  # 2 x 2 GiB
+    points = {}
+    t0 = time.time()
+    for e in range(16, 29, 2):
+        n = 1 << e
+        rows = (4 * GIB) // (8 * n)
+        g = rng.Generator(n, 1, init=False)
+        g.init()
+        g.generate_to(rows, ring.data_ptr())
+        g.sync()
+        g.profile_reset()
+        for _ in range(4):
+            g.generate_to(rows, ring.data_ptr())
+        c, t = g.profile_stat("RNG_KERNEL")
+        vpt = g.launch_config()[0]
+        g.close()
+        T = max(1, (16 * GIB) // (8 * n))
+        ck = rng.Generator(n, 1, init=False)
+        ck.init()
+        ck.generate_checksum(T)
+        ck.sync()
+        ck.init()
+        ck.profile_reset()
+        ck.generate_checksum(T)
+        ck.sync()
+        cc, ct = ck.profile_stat("CHECKSUM_KERNEL")
+        ck.close()
+        points[f"2^{e}"] = {"rows_per_launch": rows, "values_per_thread": vpt,
+                            "write_GBps": round(8 * n * rows * c / t / 1e9, 1),
+                            "checksum_values_per_s": float(f"{n * T * cc / ct:.4g}")}
+    t1 = time.time()
+    del ring
+    torch.cuda.empty_cache()
+    d = {"config": {"workload": "roofline sweep: streams 2^16..2^28 (powers of 4), seed 1, default shape; "
+                                "full-write into a 2 x 2 GiB ring vs generate-and-checksum",
+                    "l2": "4 GiB written per launch > L2: no flush needed"},
+         "points": points}
+    if clocks:
+        d["clocks"] = clocks.window(t0, t1)
+    return d
 
 
 def run_skip(args):
@@ -796,7 +1001,11 @@ def run_consumer(args, wl):
     """Host consumer threads of the streamed path: per-row XOR/sum folding
     (rng_generate_host_checksum) and copies into pageable memory through the
     staging slots, against the number of consumer threads, on the streaming
-    workload's shape (2^22 streams, 32 MiB rows); one JSON line."""
+    workload's shape (2^22 streams, 32 MiB rows); with `--consumer-chunks-mib`
+    the fold is also timed with smaller chunks (device buffers and staging
+    slots of that size, so that the slots' total footprint can fit in the
+    host's last-level cache) and `--consumer-slots` staging slots (0 = one per
+    consumer thread plus two); one JSON line."""
     import numpy as np
     import torch
     sys.path.insert(0, ROOT)
@@ -804,10 +1013,10 @@ def run_consumer(args, wl):
 
     n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
     link = measure_host_link(torch)
-    fold, copy = {}, {}
-    for k in args.consumers:
-        g = rng.Generator(n, seed, device_buffer_bytes=wl["device_buffer_bytes"], profiling=False,
-                          host_consumers=k)
+
+    def best_fold(k, chunk, slots):
+        g = rng.Generator(n, seed, device_buffer_bytes=chunk, profiling=False, host_consumers=k,
+                          host_slots=slots)
         g.generate_host_checksum(T)
         best = float("inf")
         for _ in range(args.steps):
@@ -815,8 +1024,19 @@ def run_consumer(args, wl):
             t0 = time.perf_counter()
             g.generate_host_checksum(T)
             best = min(best, time.perf_counter() - t0)
+        stats = g.host_stats()
         g.close()
-        fold[k] = 8 * n * T / best / 1e9
+        return 8 * n * T / best / 1e9, stats
+
+    fold, copy, by_chunk = {}, {}, {}
+    for k in args.consumers:
+        fold[k], _ = best_fold(k, wl["device_buffer_bytes"], 0)
+    for mib in args.consumer_chunks_mib:
+        for slots in args.consumer_slots:
+            gbs, stats = best_fold(0, mib << 20, slots)
+            by_chunk[f"{mib} MiB x {stats['slots']} slots"] = {
+                "GBps": round(gbs, 1), "slot_footprint_MiB": mib * stats["slots"], "consumers": stats["consumers"],
+                "producer_wait_frac": round(stats["producer_wait_s"] / stats["wall_s"], 3)}
     rows = min(T, 128)  # 4 GiB of pageable memory, touched before timing
     out = np.ones((rows, n), dtype=np.uint64)
     for k in args.consumers:
@@ -834,7 +1054,66 @@ def run_consumer(args, wl):
     _json_line({"workload": f"host consumers: {n} streams, 32 MiB rows; fold {T} rows, "
                             f"pageable copy {rows} rows; best of {args.steps}",
                 "unit": "GB/s", "host_link_GBps": link, "host_cores": os.cpu_count(),
-                "fold_xor_sum": fold, "pageable_copy": copy})
+                "fold_xor_sum": fold, "fold_default_consumers_by_chunk": by_chunk, "pageable_copy": copy})
+    return 0
+
+
+def run_host_dest(args, wl):
+    """Host output into three kinds of page-locked destination of the full
+    streaming step (32 GiB): rng_host_alloc with transparent huge pages,
+    cudaHostAlloc (torch pin_memory, 64 KiB pages) and rng_host_alloc with
+    base pages only.  For each: the double buffer with copy-engine reads
+    (per-chunk read times from the profiler; a chunk read below 150 GB/s
+    counts as stalled), the double buffer with copy-kernel reads and the
+    direct path, `steps` timed steps each after one warm-up step."""
+    import tempfile
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1609_01257_gb300 as rng
+
+    n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
+    nbytes = 8 * n * T
+    chunk = wl["device_buffer_bytes"]
+    link = measure_host_link(torch)
+    kinds = {}
+    for kind in ("rng_host_alloc, huge pages", "cudaHostAlloc (torch pin_memory)", "rng_host_alloc, base pages"):
+        t0 = time.perf_counter()
+        if kind.startswith("cudaHostAlloc"):
+            host = torch.empty((T, n), dtype=torch.uint64).pin_memory().numpy()
+        else:
+            host = rng.host_empty((T, n), huge_pages="huge" in kind)
+        alloc_s = time.perf_counter() - t0
+        res = {"alloc_s": round(alloc_s, 2), "huge_page_share": huge_page_share(host)}
+        for label, hp in (("double_buffer", 1), ("double_buffer_copy_kernel", 3), ("direct", 0)):
+            g = rng.Generator(n, seed, device_buffer_bytes=chunk, host_path=hp, profiling=(hp == 1), init=False)
+            g.init()
+            g.generate_to_host(T, host)
+            rates, stalled = [], []
+            for _ in range(args.steps):
+                g.init()
+                g.profile_reset()
+                t1 = time.perf_counter()
+                g.generate_to_host(T, host)
+                rates.append(round(nbytes / (time.perf_counter() - t1) / 1e9, 1))
+                if hp == 1:
+                    with tempfile.NamedTemporaryFile("r", suffix=".tsv") as f:
+                        g.profile_export(f.name)
+                        reads = [(float(a), float(b)) for q, a, b, nm in
+                                 (line.rstrip("\n").split("\t") for line in open(f.name)) if nm == "READ_BUFFER"]
+                    # exported times are in nanoseconds
+                    stalled.append(sum(1 for a, b in reads if chunk / max(b - a, 1.0) < 150.0))
+            g.close()
+            res[label] = {"GBps": rates}
+            if hp == 1:
+                res[label]["stalled_chunks"] = stalled
+                res[label]["chunks_per_step"] = (nbytes + chunk - 1) // chunk
+        kinds[kind] = res
+        del host
+        if hasattr(torch._C, "_host_emptyCache"):
+            torch._C._host_emptyCache()
+    _json_line({"workload": wl["name"] + ": host output into three kinds of page-locked destination",
+                "unit": "GB/s", "host_link_GBps": link, "chunk_bytes": chunk,
+                "stall_threshold_GBps": 150.0, "steps": args.steps, "destinations": kinds})
     return 0
 
 
@@ -868,13 +1147,19 @@ def run_queue_chart(args):
 
 
 def run_sweep(args):
-    """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread.
-    Output goes to a ring of two 2 GiB device buffers: each launch writes the
-    whole 4 GiB ring once (iterations = ring rows, no row written twice in a
-    launch, so L2 cannot absorb rewrites), four launches per point (16 GiB).
-    Launches carry the states through the state array (8 B read + 8 B written
-    per stream per launch), reported separately as `dram_GBps_incl_state`.
-    Generate-and-checksum mode is timed per stream count as well."""
+    """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread
+    1..64, full-write mode and generate-and-checksum mode.
+
+    Full-write mode: output goes to a ring of two 2 GiB device buffers; each
+    launch writes the whole 4 GiB ring once (iterations = ring rows, no row
+    written twice in a launch, so L2 cannot absorb rewrites), four launches
+    per point (16 GiB).  Launches carry the states through the state array
+    (8 B read + 8 B written per stream per launch), reported separately as
+    `dram_GBps_incl_state`.  Generate-and-checksum mode: 16 GiB worth of
+    values per point (no stores; per-row XOR and sum), for each compiled
+    values-per-thread shape.  The CPU-baseline leg times the oracle's row
+    checksums over the same rows and reports whether the GPU's checksums
+    (default shape) equal them bit for bit."""
     import torch
     sys.path.insert(0, ROOT)
     import paper_1609_01257_gb300 as rng
@@ -902,30 +1187,49 @@ def run_sweep(args):
 
         for vpt in args.sweep_vpts:
             res[vpt], res_dram[vpt], _ = point(values_per_thread=vpt)
-        cpu = None
-        if n <= (1 << 18) and not args.skip_cpu_baseline:
-            # The oracle on the same point (small stream counts): one launch's rows.
-            nb, dt = cpu_oracle_sample(n, 1, rows)
-            cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "values_per_s": nb / 8 / dt, "cores": 1,
-                   "kind": "oracle", "sample": f"{n} streams x {rows} iterations, single-threaded C oracle, {dt:.1f} s"}
         dflt, dflt_dram, cfg = point()
-        ck = rng.Generator(n, 1, init=False)
-        ck.init()
         T = max(1, (16 * GIB) // (8 * n))
-        ck.generate_checksum(T)
-        ck.sync()
-        ck.profile_reset()
-        ck.generate_checksum(T)
-        c, t = ck.profile_stat("CHECKSUM_KERNEL")
-        ck.close()
+
+        def checksum_point(**kw):
+            ck = rng.Generator(n, 1, init=False, **kw)
+            ck.init()
+            ck.generate_checksum(T)
+            ck.sync()
+            ck.init()
+            ck.profile_reset()
+            rx, rs = ck.generate_checksum(T)  # iterations 0 .. T-1
+            ck.sync()
+            c, t = ck.profile_stat("CHECKSUM_KERNEL")
+            ck.close()
+            return n * T / t, rx, rs
+
+        ck_vps = {}
+        for vpt in args.sweep_checksum_vpts:
+            ck_vps[vpt], _, _ = checksum_point(values_per_thread=vpt)
+        ck_default, rx, rs = checksum_point()
+        cpu = None
+        if not args.skip_cpu_baseline:
+            # The oracle on the same rows: its row checksums, timed on one
+            # host core, and compared with the GPU's.
+            import oracle  # test infrastructure: the CPU baseline leg only
+            oracle.build()
+            t0 = time.perf_counter()
+            wx, ws_, _ = oracle.row_checksums(n, 1, T)
+            dt = time.perf_counter() - t0
+            same = bool(np.array_equal(rx.cpu().numpy(), wx) and np.array_equal(rs.cpu().numpy(), ws_))
+            cpu = {"value": n * T / dt, "unit": "values/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{n} streams x {T} iterations, row checksums, single-threaded C oracle, {dt:.1f} s",
+                   "checksums_equal_gpu": same}
         _json_line({"sweep_streams": n, "rows_per_launch": rows, "launches": launches,
                     "write_GBps_by_vpt": {str(k): round(v, 1) for k, v in res.items()},
                     "dram_GBps_incl_state_by_vpt": {str(k): round(v, 1) for k, v in res_dram.items()},
                     "default_shape": {"vpt": cfg[0], "grid": cfg[2], "GBps": round(dflt, 1),
                                       "dram_GBps_incl_state": round(dflt_dram, 1)},
-                    "cpu_baseline": cpu,
-                    "checksum_iterations": T, "checksum_values_per_s": n * T / t,
-                    "checksum_equiv_GBps": 8 * n * T / t / 1e9})
+                    "checksum_iterations": T,
+                    "checksum_values_per_s_by_vpt": {str(k): float(f"{v:.4g}") for k, v in ck_vps.items()},
+                    "checksum_values_per_s": ck_default,
+                    "checksum_equiv_GBps": 8 * ck_default / 1e9,
+                    "cpu_baseline": cpu})
     return 0
 
 
@@ -935,7 +1239,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart", "consumer", "skip"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "served", "sweep", "checksum", "queue-chart", "consumer", "skip", "host-dest"],
                     default="streaming")
     ap.add_argument("--duration", type=float, default=60.0, help="served workload length in seconds")
     ap.add_argument("--batch-cap-gib", type=float, default=8.0, help="batched: total output cap")
@@ -945,16 +1249,23 @@ def main(argv=None):
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
     ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
     ap.add_argument("--server-mode", type=int, default=2, help="served: 1 one unit per block, 2 persistent")
-    ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 64])
+    ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64])
+    ap.add_argument("--sweep-checksum-vpts", type=int, nargs="+", default=[1, 2, 4, 8, 16, 32, 64])
     ap.add_argument("--skip-streams", type=int, nargs="+", default=[1 << 22, 1 << 26, 1 << 28],
                     help="skip: stream counts")
     ap.add_argument("--consumers", type=int, nargs="+", default=[1, 2, 4, 8, 16],
                     help="consumer: host consumer thread counts")
+    ap.add_argument("--consumer-chunks-mib", type=int, nargs="+", default=[32],
+                    help="consumer: chunk (device buffer and staging slot) sizes for the default-thread fold")
+    ap.add_argument("--consumer-slots", type=int, nargs="+", default=[0],
+                    help="consumer: staging slot counts for the chunk sweep (0 = consumers + 2)")
     ap.add_argument("--output-mode", type=int, choices=[0, 1], default=0,
                     help="streaming/checksum: 0 the paper's output, 1 xorshift64* scrambled values")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="default workload: leave out the plain, batched, checksum, sweep and served objects")
     ap.add_argument("--cpu-rows", type=int, default=0,
                     help="iterations in the CPU-baseline sample (0 = the whole workload)")
     ap.add_argument("--reference-rows", type=int, default=128, help="iterations per reference step")
@@ -983,7 +1294,7 @@ def main(argv=None):
         return run_queue_chart(args)
     if args.workload == "skip":
         return run_skip(args)
-    wl = dict(WORKLOADS["streaming" if args.workload in ("checksum", "consumer") else args.workload])
+    wl = dict(WORKLOADS["streaming" if args.workload in ("checksum", "consumer", "host-dest") else args.workload])
     if args.iterations:
         wl["iterations"] = args.iterations
         wl["name"] = re.sub(r"x \d+ iterations", f"x {args.iterations} iterations", wl["name"])
@@ -991,6 +1302,8 @@ def main(argv=None):
         return run_checksum(args, wl)
     if args.workload == "consumer":
         return run_consumer(args, wl)
+    if args.workload == "host-dest":
+        return run_host_dest(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

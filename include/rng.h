@@ -308,6 +308,32 @@ int rng_launch_config(const rng_gen *g, uint32_t *values_per_thread,
 void rng_destroy(rng_gen *g);
 
 /* ------------------------------------------------------------------ */
+/* Page-locked host memory for host output (Section 5)                 */
+/* ------------------------------------------------------------------ */
+/* Section 5 reads every generated batch into host memory.  This allocates
+ * `bytes` of zero-filled, page-locked host memory (registered with CUDA, so
+ * rng_generate's double buffer copies into it directly and its direct path
+ * stores into it over the host link) and returns its address in *out.
+ * With RNG_HOST_HUGE_PAGES in `flags` the range is aligned to the kernel's
+ * transparent huge-page size and asks the kernel for huge pages
+ * (MADV_HUGEPAGE); without it, base pages only.  On Grace-Blackwell the
+ * GPU's write rate into a large destination depends on these pages: into
+ * 64 KiB pages (as cudaHostAlloc returns them) copies of 32 MiB stall
+ * intermittently for whichever engine moves the bytes, into 512 MiB huge
+ * pages they run at the link rate.  Where the kernel has transparent huge
+ * pages disabled the range keeps base pages.  The memory is owned by the
+ * caller and released with rng_host_free; every page is faulted in before
+ * the call returns, so it blocks for about a second per 32 GiB.  Errors:
+ * RNG_EINVAL (NULL out, zero bytes, unknown flags), RNG_ENOMEM (the mapping
+ * failed), RNG_ECUDA / RNG_ENOMEM (page-locking failed; nothing is kept). */
+#define RNG_HOST_HUGE_PAGES 1u
+int rng_host_alloc(size_t bytes, uint32_t flags, void **out, rng_err **err);
+
+/* Releases memory from rng_host_alloc (unregisters and unmaps it).  NULL is
+ * a no-op; any other address not returned by rng_host_alloc is RNG_EINVAL. */
+int rng_host_free(void *p);
+
+/* ------------------------------------------------------------------ */
 /* Profiler (Section 3.3 and the profiling summary of Section 4.1)     */
 /* ------------------------------------------------------------------ */
 typedef struct rng_prof rng_prof;
@@ -411,40 +437,44 @@ void rng_batch_destroy(rng_batch *b);
 /* Batched generation without allocation                               */
 /* ------------------------------------------------------------------ */
 /* The paper has no counterpart to this entry point.  It is for callers that
- * cannot call cudaMalloc: code that runs while someone else is capturing a
- * CUDA stream into a graph, code inside a framework whose memory pool owns
- * the device, or latency-bound code that cannot pay for an allocation (or
- * the device-wide synchronisation of a cudaFree) on every call.
+ * cannot call cudaMalloc: code inside a framework whose memory pool owns the
+ * whole device and forbids allocations beside it, or latency-bound code that
+ * cannot pay for an allocation (or the device-wide synchronisation of a
+ * cudaFree) on every call.
  *
  * It produces exactly what rng_batch_create + rng_batch_run produce for the
  * same instances (iterations 0 .. iterations[k]-1 of instance k into outs[k],
- * iteration-major), with one launch of the same work-list kernel, but it
- * allocates nothing: no cudaMalloc, cudaFree, pinned or host heap memory and
- * no CUDA graph.  Its scratch -- the kernel's work counter and work tables --
- * is one fixed array of RNG_NOALLOC_SCRATCH_BYTES in device global memory
- * that every GPU loading this library holds until the process exits.
+ * iteration-major), with one launch of the served form's work-list kernel
+ * (an instance table, a unit table and a work counter), but it allocates
+ * nothing: no cudaMalloc, cudaFree, pinned or host heap memory and no CUDA
+ * graph.  Its scratch -- the counter and the two tables -- is one fixed array
+ * of RNG_NOALLOC_SCRATCH_BYTES in device global memory that every GPU loading
+ * this library holds until the process exits.
  *
  * Limits: at most RNG_NOALLOC_MAX_INSTANCES instances and
  * RNG_NOALLOC_MAX_UNITS work units, one unit per started group of 2048
  * streams of an instance (sum over k of ceil(streams[k] / 2048)); larger
- * batches are rejected with RNG_EINVAL and a message naming the limit.
+ * batches are rejected with RNG_EINVAL and a message naming the limit,
+ * before anything is queued.
  *
  * Arguments are those of rng_batch_create (host arrays of `count` entries;
  * outs[k] caller-owned device memory of 8*streams[k]*iterations[k] bytes,
  * 8-byte aligned); `stream` is the cudaStream_t to launch on (NULL = the
- * legacy default stream).  The call is asynchronous: it returns after
- * queueing a table upload, a reset of the counter and the kernel on
- * `stream`.
+ * legacy default stream).  The call queues a table upload, a reset of the
+ * counter and the kernel on `stream` and returns without waiting for the
+ * kernel.  The tables are uploaded from pageable host memory, so the call
+ * may wait for work already queued on `stream` before it returns.
  *
  * The first call on a device, with that device current, looks up the
- * scratch array's device address (cudaGetSymbolAddress) and caches it; make
- * that first call before any stream capture begins.  A cudaDeviceReset
- * destroys the array with the context, so do not call this entry point again
- * on a device after resetting it in the same process.  All calls share the one
- * array and each call overwrites it, so calls whose work overlaps on the GPU
- * (launched on different streams without ordering between them) race and
- * produce wrong output; calls on one stream are ordered and safe.  The host
- * side of concurrent calls is serialised by a lock. */
+ * scratch array's device address (cudaGetSymbolAddress) and caches it; this
+ * may make the driver load the library's device code.  Make that first call
+ * before any stream capture begins.  A cudaDeviceReset destroys the array with
+ * the context, so do not call this entry point again on a device after
+ * resetting it in the same process.  All calls share the one array and each
+ * call overwrites it, so calls whose work overlaps on the GPU (launched on
+ * different streams without ordering between them) race and produce wrong
+ * output; calls on one stream are ordered and safe.  The host side of
+ * concurrent calls is serialised by a lock. */
 #define RNG_NOALLOC_MAX_INSTANCES 4096u
 #define RNG_NOALLOC_MAX_UNITS 262144u
 #define RNG_NOALLOC_SCRATCH_BYTES \

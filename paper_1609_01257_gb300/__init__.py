@@ -13,6 +13,7 @@ from .builder import build  # noqa: F401
 from .generator import Generator, Profiler  # noqa: F401
 from .batch import Batch  # noqa: F401
 from .serve import Server, run_load  # noqa: F401
+from .hostmem import host_empty  # noqa: F401
 
 
 def launch_count() -> int:

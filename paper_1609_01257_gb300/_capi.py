@@ -22,6 +22,7 @@ P_u64 = ctypes.POINTER(ctypes.c_uint64)
 
 RNG_OK, RNG_EINVAL, RNG_ENOMEM, RNG_ECUDA, RNG_ESTATE, RNG_ETIMEOUT, RNG_EBUDGET, RNG_ESINK = range(8)
 RNG_PROF_SORT_NAME, RNG_PROF_SORT_TIME, RNG_PROF_SORT_DESC = 0, 1, 0x10
+RNG_HOST_HUGE_PAGES = 1
 
 
 class RngErr(ctypes.Structure):
@@ -165,6 +166,8 @@ SIGNATURES = {
     "rng_server_release": ([c_vp, c_u64, P_err], c_int),
     "rng_server_get_stats": ([c_vp, ctypes.POINTER(RngServerStats)], c_int),
     "rng_server_destroy": ([c_vp], None),
+    "rng_host_alloc": ([ctypes.c_size_t, c_u32, ctypes.POINTER(c_vp), P_err], c_int),
+    "rng_host_free": ([c_vp], c_int),
 }
 
 

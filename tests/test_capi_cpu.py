@@ -275,3 +275,22 @@ def test_alternative_output_mode_shapes_are_checked_on_the_host(L):
     for vpt, block in [(6, 0), (12, 0), (8, 128)]:
         o.values_per_thread, o.block_threads = vpt, block
         assert L.rng_create(4096, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL, (vpt, block)
+
+
+def test_host_alloc_rejects_bad_arguments_without_a_gpu(L):
+    # Argument checks of the page-locked host allocator come before any
+    # mapping or CUDA call; freeing NULL is a no-op and an address the
+    # allocator did not return is refused.
+    err = ctypes.POINTER(C.RngErr)()
+    p = ctypes.c_void_p()
+    assert L.rng_host_alloc(16, C.RNG_HOST_HUGE_PAGES, None, ctypes.byref(err)) == C.RNG_EINVAL
+    L.rng_err_clear(ctypes.byref(err))
+    assert L.rng_host_alloc(0, C.RNG_HOST_HUGE_PAGES, ctypes.byref(p), ctypes.byref(err)) == C.RNG_EINVAL
+    assert b"zero bytes" in err.contents.msg and not p
+    L.rng_err_clear(ctypes.byref(err))
+    assert L.rng_host_alloc(16, 6, ctypes.byref(p), ctypes.byref(err)) == C.RNG_EINVAL
+    assert b"flags" in err.contents.msg
+    L.rng_err_clear(ctypes.byref(err))
+    assert L.rng_host_free(None) == C.RNG_OK
+    buf = ctypes.create_string_buffer(64)
+    assert L.rng_host_free(ctypes.cast(buf, ctypes.c_void_p)) == C.RNG_EINVAL
