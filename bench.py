@@ -394,10 +394,15 @@ def run_gpu(args, wl):
             barrier()
             g.profile_reset()
             t0 = time.perf_counter()
+            marks = [t0]
             for _ in range(steps):
                 step_host()
+                marks.append(time.perf_counter())
             barrier()
+            step_ms.append([round(1e3 * (b - a), 1) for a, b in zip(marks, marks[1:])])
             return max_over_ranks(time.perf_counter() - t0), g.profile()
+
+        step_ms = []  # per-step host times of each leg, in the order the legs run
 
         # Default host path: the kernel stores straight into the page-locked
         # buffer over the host link.
@@ -406,7 +411,7 @@ def run_gpu(args, wl):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes,
                "steps": args.e2e_steps, "ms_per_step": 1e3 * host_s / args.e2e_steps,
                "path": "direct stores into page-locked host memory",
-               "iterations_per_call": rows, "destination": dest}
+               "iterations_per_call": rows, "destination": dest, "step_ms": step_ms[0]}
         # The paper's double buffer: two device buffers, copy engine reads.
         # Timed without the event profiler; one more profiled step gives the
         # kernel/read/overlap split.
@@ -420,7 +425,7 @@ def run_gpu(args, wl):
         gdb.close()
         e2e["double_buffer"] = {
             "value": nbytes * ws * args.e2e_steps / db_s / 1e9, "unit": "GB/s",
-            "ms_per_step": 1e3 * db_s / args.e2e_steps,
+            "ms_per_step": 1e3 * db_s / args.e2e_steps, "step_ms": step_ms[1],
             "profiled_step": {"read_buffer_s": prof["aggregate"].get("READ_BUFFER", (0, 0))[0],
                               "rng_kernel_s": prof["aggregate"].get("RNG_KERNEL", (0, 0))[0],
                               "overlap_s": sum(prof["overlaps"].values())}}
@@ -430,7 +435,7 @@ def run_gpu(args, wl):
         sm_s, _ = host_leg(gsm, args.e2e_steps)
         gsm.close()
         e2e["double_buffer_copy_kernel"] = {"value": nbytes * ws * args.e2e_steps / sm_s / 1e9, "unit": "GB/s",
-                                            "ms_per_step": 1e3 * sm_s / args.e2e_steps}
+                                            "ms_per_step": 1e3 * sm_s / args.e2e_steps, "step_ms": step_ms[-1]}
         e2e["host_link_GBps"] = link
         e2e["frac_link"] = e2e["value"] / link
         del host
@@ -1014,9 +1019,9 @@ def run_consumer(args, wl):
     n, T, seed = wl["streams"], wl["iterations"], wl["seed"]
     link = measure_host_link(torch)
 
-    def best_fold(k, chunk, slots):
+    def best_fold(k, chunk, slots, host_path=0):
         g = rng.Generator(n, seed, device_buffer_bytes=chunk, profiling=False, host_consumers=k,
-                          host_slots=slots)
+                          host_slots=slots, host_path=host_path)
         g.generate_host_checksum(T)
         best = float("inf")
         for _ in range(args.steps):
@@ -1031,12 +1036,13 @@ def run_consumer(args, wl):
     fold, copy, by_chunk = {}, {}, {}
     for k in args.consumers:
         fold[k], _ = best_fold(k, wl["device_buffer_bytes"], 0)
-    for mib in args.consumer_chunks_mib:
-        for slots in args.consumer_slots:
-            gbs, stats = best_fold(0, mib << 20, slots)
-            by_chunk[f"{mib} MiB x {stats['slots']} slots"] = {
-                "GBps": round(gbs, 1), "slot_footprint_MiB": mib * stats["slots"], "consumers": stats["consumers"],
-                "producer_wait_frac": round(stats["producer_wait_s"] / stats["wall_s"], 3)}
+    paths = {0: "copy engine", 2: "kernel stores into the slots", 3: "copy kernel"}
+    for hp, mib, slots in ((hp, mib, slots) for hp in args.consumer_host_paths
+                           for mib in args.consumer_chunks_mib for slots in args.consumer_slots):
+        gbs, stats = best_fold(0, mib << 20, slots, hp)
+        by_chunk[f"{paths.get(hp, hp)}: {mib} MiB x {stats['slots']} slots"] = {
+            "GBps": round(gbs, 1), "slot_footprint_MiB": mib * stats["slots"], "consumers": stats["consumers"],
+            "producer_wait_frac": round(stats["producer_wait_s"] / stats["wall_s"], 3)}
     rows = min(T, 128)  # 4 GiB of pageable memory, touched before timing
     out = np.ones((rows, n), dtype=np.uint64)
     for k in args.consumers:
@@ -1257,11 +1263,13 @@ def main(argv=None):
                     help="consumer: host consumer thread counts")
     ap.add_argument("--consumer-chunks-mib", type=int, nargs="+", default=[32],
                     help="consumer: chunk (device buffer and staging slot) sizes for the default-thread fold")
+    ap.add_argument("--consumer-host-paths", type=int, nargs="+", default=[0],
+                    help="consumer: host paths for the chunk sweep (0 copy engine, 2 kernel into the slots, 3 copy kernel)")
     ap.add_argument("--consumer-slots", type=int, nargs="+", default=[0],
                     help="consumer: staging slot counts for the chunk sweep (0 = consumers + 2)")
     ap.add_argument("--output-mode", type=int, choices=[0, 1], default=0,
                     help="streaming/checksum: 0 the paper's output, 1 xorshift64* scrambled values")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-configs", action="store_true",

@@ -116,8 +116,12 @@ typedef struct rng_opts {
                                      storing into page-locked memory or the
                                      staging slots) instead of the copy engine.
                                      Sinks, file descriptors and host checksums
-                                     use the double buffer in every mode, with
-                                     copy-kernel reads in mode 3 */
+                                     go through page-locked staging slots: in
+                                     modes 0 and 1 by the double buffer with
+                                     copy-engine reads, in mode 3 with
+                                     copy-kernel reads, and in mode 2 the
+                                     kernel stores each chunk straight into
+                                     its slot (no device buffer, no copy) */
     uint32_t host_consumers;      /* host threads draining the staging slots
                                      (at most 64).  0 (default): one for sinks
                                      (in order); for pageable copies and host

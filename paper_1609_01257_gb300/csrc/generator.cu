@@ -307,6 +307,7 @@ struct Target {
   uint64_t *row_sum = nullptr;
   unsigned consumers = 1;        // host threads draining the slots
   bool sm_copy = false;          // reads by a copy kernel instead of the copy engine
+  bool direct = false;           // the kernel stores each chunk into its staging slot (no device buffer, no copy)
 };
 
 // XOR and wrapping sum of `n` values; four independent lanes so that the
@@ -507,6 +508,20 @@ int double_buffer_host(rng_gen *g, uint64_t T, Target tgt, rng_err **err) {
       cons.slot_free[slot] = false;
     }
     cudaError_t st = cudaSuccess;
+    if (tgt.direct && staged) {
+      // The kernel writes the chunk straight into its staging slot over the
+      // host link; the slot is ready once the kernel has finished.
+      status = launch_chunk(g, ck, hash_first_rows && ck.r0 == 0, static_cast<uint64_t *>(g->h_slots_dev[slot]), err);
+      if (status) break;
+      st = cudaEventRecord(g->slot_ready[slot], g->compute);
+      if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "event record"); break; }
+      {
+        std::lock_guard<std::mutex> lk(cons.mu);
+        cons.jobs.push_back({ck, slot, false});
+      }
+      cons.cv.notify_all();
+      continue;
+    }
     if (c >= 2) st = cudaStreamWaitEvent(g->compute, g->copied[b], 0);
     if (st != cudaSuccess) { status = rngi::cuda_fail(err, st, "cudaStreamWaitEvent"); break; }
     status = launch_chunk(g, ck, hash_first_rows && ck.r0 == 0, g->d_buf[b], err);
@@ -854,6 +869,7 @@ int rng_generate_sink(rng_gen *g, uint64_t iterations, rng_sink_fn sink, void *u
   tgt.user = user;
   tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : 1;
   tgt.sm_copy = g->opts.host_path == 3;
+  tgt.direct = g->opts.host_path == 2;
   return double_buffer_host(g, iterations, tgt, err);
 }
 
@@ -890,6 +906,7 @@ int rng_generate_fd(rng_gen *g, uint64_t iterations, int fd, rng_err **err) {
   tgt.user = &user;
   tgt.consumers = 1;  // the bytes must reach the descriptor in order
   tgt.sm_copy = g->opts.host_path == 3;
+  tgt.direct = g->opts.host_path == 2;
   return double_buffer_host(g, iterations, tgt, err);
 }
 
@@ -911,6 +928,7 @@ int rng_generate_host_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xo
   tgt.row_sum = row_sum_host;
   tgt.consumers = g->opts.host_consumers ? g->opts.host_consumers : auto_consumers();
   tgt.sm_copy = g->opts.host_path == 3;
+  tgt.direct = g->opts.host_path == 2;
   return double_buffer_host(g, iterations, tgt, err);
 }
 

@@ -26,9 +26,10 @@ CASES = [
 
 
 @pytest.mark.parametrize("n,T,buf", CASES)
-@pytest.mark.parametrize("consumers,host_path", [(1, 0), (3, 0), (8, 0), (3, 3)])
+@pytest.mark.parametrize("consumers,host_path", [(1, 0), (3, 0), (8, 0), (3, 3), (1, 2), (3, 2)])
 def test_host_checksum_matches_oracle(n, T, buf, consumers, host_path):
-    # host_path 3: the slots are filled by a copy kernel instead of the copy engine.
+    # host_path 3: the slots are filled by a copy kernel instead of the copy
+    # engine; host_path 2: the kernel stores each chunk straight into its slot.
     g = rng.Generator(n, 21, device_buffer_bytes=buf, host_consumers=consumers, host_path=host_path)
     rx, rs = g.generate_host_checksum(T)
     tail = g.generate(2).cpu().numpy()  # the streams advanced by T
@@ -98,7 +99,7 @@ def test_pageable_copy_with_consumers(consumers, host_path):
     assert np.array_equal(out, oracle.generate(n, 8, T))
 
 
-@pytest.mark.parametrize("host_path", [0, 3])
+@pytest.mark.parametrize("host_path", [0, 2, 3])
 def test_fd_output_in_order_with_consumers(tmp_path, host_path):
     # rng_generate_fd keeps one consumer whatever host_consumers says: the
     # bytes reach the file in stream order.
@@ -110,6 +111,31 @@ def test_fd_output_in_order_with_consumers(tmp_path, host_path):
     g.close()
     got = np.fromfile(path, dtype=np.uint64).reshape(T, n)
     assert np.array_equal(got, oracle.generate(n, 4, T))
+
+
+@pytest.mark.parametrize("consumers", [1, 4])
+def test_sink_with_chunks_stored_straight_into_the_slots(consumers):
+    # host_path 2: no device buffer and no copy -- one kernel per chunk
+    # writes the slot over the host link, then a consumer hands it on.
+    n, T = 4099, 31
+    g = rng.Generator(n, 17, device_buffer_bytes=8 * n * 4, host_path=2, host_consumers=consumers)
+    got = np.zeros((T, n), dtype=np.uint64)
+    order = []
+
+    def sink(first_it, block, first_stream):
+        order.append(first_it)
+        got[first_it:first_it + block.shape[0], first_stream:first_stream + block.shape[1]] = block
+
+    g.profile_reset()
+    g.generate_sink(T, sink)
+    kernels, _ = g.profile_stat("RNG_KERNEL")
+    reads, _ = g.profile_stat("READ_BUFFER")
+    g.close()
+    assert (kernels, reads) == (8, 0)
+    if consumers == 1:
+        assert order == list(range(0, T, 4))
+    assert sorted(order) == list(range(0, T, 4))
+    assert np.array_equal(got, oracle.generate(n, 17, T))
 
 
 def test_host_consumers_bound():
