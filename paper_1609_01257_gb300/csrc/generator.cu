@@ -958,7 +958,8 @@ int rng_generate_checksum(rng_gen *g, uint64_t iterations, uint64_t *row_xor_dev
   a.write_state = 1;
   a.state_out = a.state;
   const uint32_t v = g->opts.values_per_thread;
-  const uint32_t vpt = rngi::checksum_vpt(g->n, (v && (v & (v - 1)) == 0 && v <= 64) ? v : 0, g->device);
+  const uint32_t vpt = rngi::checksum_vpt(g->n, (v && (v & (v - 1)) == 0 && v <= 64) ? v : 0, g->device,
+                                           g->opts.output_mode);
   // Few tiles, many rows: bands, as for the row kernel.
   rngi::LaunchShape sh{};
   sh.vpt = vpt;

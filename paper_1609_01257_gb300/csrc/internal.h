@@ -91,7 +91,7 @@ cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t 
                         const uint64_t *cols, cudaStream_t st);
 // Values per thread of a generate-and-checksum launch over `span` streams
 // (vpt = 0: choose; else a power of two up to 64).
-uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device);
+uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device, uint32_t out_mode);
 // Generate-and-checksum launch with `vpt` values per thread; a.band_rows != 0
 // selects the banded variant (a.jump, a.state_out as for the row kernel).
 cudaError_t launch_checksum(const RowsLaunch &a, uint32_t vpt, uint64_t *row_xor, uint64_t *row_sum,

@@ -138,6 +138,53 @@ __device__ __forceinline__ void store_tile_state(const uint64_t (&st)[VPT], uint
     }
 }
 
+// Rows of one tile whose segments do not start on 128-byte lines (the row
+// pitch is not a multiple of 16 values, or the output is not line aligned).
+// A warp-wide run of 8-byte stores that starts off a line touches nine
+// 32-byte sectors instead of eight, which costs about an eighth of the write
+// rate over whole rows.  So each row is staged in shared memory (the
+// thread's values at their places in the tile, two buffers used in turn, one
+// barrier per row) and stored as 16-byte pieces aligned to the lines, with
+// 8-byte stores for the ragged head and tail of the segment.  Values past
+// `span` are staged but not stored.  Every thread of the block must call it.
+template <int VPT>
+__host__ __device__ constexpr int staged_words() {
+  return VPT <= 8 ? 2 * kBlock * VPT : 2;  // 2 x tile (up to 32 KiB); larger tiles store directly
+}
+
+template <int VPT, int OUT = 0>
+__device__ __forceinline__ void emit_rows_staged(uint64_t (&st)[VPT], uint64_t *row, uint64_t pitch,
+                                                 uint64_t rows, uint64_t span, uint64_t *buf) {
+  constexpr int kTile = kBlock * VPT;
+  const int n = span < static_cast<uint64_t>(kTile) ? static_cast<int>(span) : kTile;
+  for (uint64_t r = 0; r < rows; ++r) {
+    uint64_t *b = buf + (r & 1) * kTile;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) b[threadIdx.x + kBlock * j] = prng::emitted<OUT>(st[j]);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+    __syncthreads();
+    // Values before the segment's first line boundary, then line-aligned pairs.
+    const int mis = static_cast<int>((reinterpret_cast<uintptr_t>(row) >> 3) & 15);
+    const int h = min(n, (16 - mis) & 15);
+    if (static_cast<int>(threadIdx.x) < h) store_one<kPolicyStreaming>(row + threadIdx.x, b[threadIdx.x]);
+    const int pairs = (n - h) >> 1;
+    for (int c = threadIdx.x; c < pairs; c += kBlock) {
+      const int k = h + 2 * c;
+      store_pair<kPolicyStreaming>(row + k, b[k], b[k + 1]);
+    }
+    if (((n - h) & 1) && threadIdx.x == 0) store_one<kPolicyStreaming>(row + n - 1, b[n - 1]);
+    row += pitch;
+  }
+  __syncthreads();  // the buffers are free for the next tile or unit
+}
+
+// Whether every row of a segment starting at `row0` with pitch `pitch` starts
+// on a 128-byte line.
+__device__ __forceinline__ bool rows_line_aligned(const uint64_t *row0, uint64_t pitch) {
+  return (reinterpret_cast<uintptr_t>(row0) & 127) == 0 && (pitch & 15) == 0;
+}
+
 // Nibble tables of a 64x64 matrix over GF(2) given by its columns (col[j] =
 // image of bit j): tab[q][e] = XOR of columns 4q+i over the bits i set in the
 // 4-bit value e.  The product with a vector is then 16 table reads and XORs
@@ -360,7 +407,7 @@ __global__ void __launch_bounds__(kBlock) checksum_kernel(const RowsLaunch a,
 // units carry similar numbers of bytes.
 template <int VPT>
 __device__ __forceinline__ void process_unit(const BatchInstance *__restrict__ inst,
-                                             const BatchUnit *__restrict__ units, uint32_t u) {
+                                             const BatchUnit *__restrict__ units, uint32_t u, uint64_t *stage) {
   const BatchUnit wu = units[u];
   const BatchInstance in = inst[wu.inst];
   const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
@@ -379,10 +426,15 @@ __device__ __forceinline__ void process_unit(const BatchInstance *__restrict__ i
     a.ring_rows = 0;
     const uint64_t span = wu.count - off;
     uint64_t *row = in.out + a.s_begin;
-    // 16-byte stores for few values per thread on aligned rows; one
-    // streaming 8-byte store per value otherwise (the faster form once a
-    // thread holds six or more streams).
-    if (VPT % 2 == 0 && VPT < 6 && in.vec) {
+    // Rows off the 128-byte lines: staged through shared memory.  Otherwise
+    // 16-byte stores for few values per thread on aligned rows, one
+    // streaming 8-byte store per value from six values per thread up.
+    if (staged_words<VPT>() > 2 && !rows_line_aligned(row, a.pitch)) {
+      uint64_t st[VPT];
+      load_tile<VPT, 1>(st, a, 0, span);
+      emit_rows_staged<VPT>(st, row, a.pitch, a.rows, span, stage);
+      if (a.write_state) store_tile_state<VPT, 1>(st, a.state, a, 0, span);
+    } else if (VPT % 2 == 0 && VPT < 6 && in.vec) {
       constexpr int V2 = VPT >= 2 ? VPT : 2;
       uint64_t st[V2];
       load_tile<V2, 2>(st, a, 0, span);
@@ -412,8 +464,9 @@ template <int VPT>
 __global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *__restrict__ inst,
                                                           const BatchUnit *__restrict__ units,
                                                           uint32_t n_units, uint32_t *counter) {
+  __shared__ uint64_t stage[staged_words<VPT>()];
   if (counter == nullptr) {
-    if (blockIdx.x < n_units) process_unit<VPT>(inst, units, blockIdx.x);
+    if (blockIdx.x < n_units) process_unit<VPT>(inst, units, blockIdx.x, stage);
     return;
   }
   __shared__ uint32_t s_unit;
@@ -423,14 +476,14 @@ __global__ void __launch_bounds__(kBlock) worklist_kernel(const BatchInstance *_
     const uint32_t u = s_unit;
     __syncthreads();
     if (u >= n_units) return;
-    process_unit<VPT>(inst, units, u);
+    process_unit<VPT>(inst, units, u, stage);
   }
 }
 
 // Batched form over self-contained units (see BatchWork): every unit starts
 // from the id hash and writes all rows of one tile of one instance.
 template <int VPT>
-__device__ __forceinline__ void process_work(const BatchWork &w) {
+__device__ __forceinline__ void process_work(const BatchWork &w, uint64_t *stage) {
   RowsLaunch a;
   a.state = nullptr;
   a.out = w.out;
@@ -446,7 +499,11 @@ __device__ __forceinline__ void process_work(const BatchWork &w) {
   const uint64_t span = w.count;
   const uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
   uint64_t *row = w.out + w.s_begin;
-  if (VPT % 2 == 0 && VPT < 6 && w.vec) {
+  if (staged_words<VPT>() > 2 && !rows_line_aligned(row, a.pitch)) {
+    uint64_t st[VPT];
+    load_tile<VPT, 1>(st, a, 0, span);
+    emit_rows_staged<VPT>(st, row, a.pitch, a.rows, span, stage);
+  } else if (VPT % 2 == 0 && VPT < 6 && w.vec) {
     constexpr int V2 = VPT >= 2 ? VPT : 2;
     uint64_t st[V2];
     load_tile<V2, 2>(st, a, 0, span);
@@ -467,10 +524,11 @@ __device__ __forceinline__ void process_work(const BatchWork &w) {
 template <int VPT>
 __global__ void __launch_bounds__(kBlock) batch_work_kernel(const BatchWork *__restrict__ work, uint32_t n,
                                                             uint32_t *counter) {
+  __shared__ uint64_t stage[staged_words<VPT>()];
   if (counter == nullptr) {
     if (blockIdx.x < n) {
       const BatchWork w = work[blockIdx.x];
-      process_work<VPT>(w);
+      process_work<VPT>(w, stage);
     }
     return;
   }
@@ -482,7 +540,7 @@ __global__ void __launch_bounds__(kBlock) batch_work_kernel(const BatchWork *__r
     __syncthreads();
     if (u >= n) return;
     const BatchWork w = work[u];
-    process_work<VPT>(w);
+    process_work<VPT>(w, stage);
   }
 }
 

@@ -259,13 +259,17 @@ cudaError_t launch_jump(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t 
   return e;
 }
 
-uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device) {
+uint32_t checksum_vpt(uint64_t span, uint32_t vpt, int device, uint32_t out_mode) {
   (void)device;
   if (vpt) return vpt;
   // 16 values per thread amortise the per-row reductions best (2^22 and 2^26
   // streams: 1.72e12 values/s at 16, 1.38e12 at 8); runs with few tiles are
   // banded to fill the GPU (2^18 streams: 1.21e12 banded at 16 vs 0.83e12
-  // unbanded at 8).  Smaller values only when one tile would be mostly empty.
+  // unbanded at 8).  Up to 2^18 streams (banded launches) 32 are faster
+  // still in output mode 0 (2^16 and 2^18 streams: 1.73e12 at 32, 1.64e12 at
+  // 16; from 2^20 streams 16 is best: 1.55e12 vs 1.47e12 at 32).  Smaller
+  // values only when one tile would be mostly empty.
+  if (out_mode == 0 && span <= (uint64_t(1) << 18) && span >= uint64_t(kGenBlock) * 32) return 32;
   for (uint32_t v = 16; v >= 2; v /= 2)
     if (span >= uint64_t(kGenBlock) * v) return v;
   return 1;

@@ -66,6 +66,38 @@ def test_unaligned_instance_outputs():
     b.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("vpt", [1, 2, 4, 6, 8])
+def test_rows_off_the_cache_lines_are_staged(vpt, mode):
+    # Row pitches that are not multiples of 16 values and outputs that start
+    # off a 128-byte line: these rows go through the shared-memory staging.
+    # Several tiles per instance, ragged last tiles, every output surrounded
+    # by canary values that must stay untouched.
+    streams = [2049, 4097, 70_001, 1000, 4103, 16, 5000]
+    iters = [5, 3, 2, 9, 4, 7, 3]
+    seeds = [3, 1, 4, 1, 5, 9, 2]
+    offsets = [1, 3, 5, 7, 16, 9, 2]     # 8-byte words from a line boundary
+    total = sum(o + n * t + 3 for o, n, t in zip(offsets, streams, iters))
+    buf = torch.full((total + 16,), 0x5A5A, dtype=torch.int64, device="cuda").view(torch.uint64)
+    outs, spans, pos = [], [], 0
+    for o, n, t in zip(offsets, streams, iters):
+        pos += o
+        outs.append(buf[pos:pos + n * t].view(t, n))
+        spans.append((pos, pos + n * t))
+        pos += n * t + 3
+    b = rng.Batch(streams, iters, seeds, outputs=outs, values_per_thread=vpt, mode=mode)
+    b.run()
+    b.sync()
+    for k in range(len(streams)):
+        assert np.array_equal(outs[k].cpu().numpy(), oracle.generate(streams[k], seeds[k], iters[k])), k
+    host = buf.view(torch.int64).cpu().numpy()
+    mask = np.ones(host.size, dtype=bool)
+    for a, e in spans:
+        mask[a:e] = False
+    assert (host[mask] == 0x5A5A).all()
+    b.close()
+
+
 def _row_checksums(block):
     return np.bitwise_xor.reduce(block, axis=1), block.sum(axis=1, dtype=np.uint64)
 

@@ -337,7 +337,10 @@ def test_few_streams_many_rows_shapes_without_banded_variant(vpt):
     assert np.array_equal(got, oracle.generate(n, 29, T))
 
 
-@pytest.mark.parametrize("n,T", [(1, 3000), (100, 1000), (4097, 700), (1 << 16, 300)])
+# Up to 2^18 streams the default shape holds 32 values per thread (8192 is the
+# smallest such run: one tile); 200,003 ends on a ragged tile.
+@pytest.mark.parametrize("n,T", [(1, 3000), (100, 1000), (4097, 700), (8192, 500), (1 << 16, 300),
+                                 (200_003, 60)])
 def test_checksum_mode_banded(n, T):
     g = rng.Generator(n, 31)
     rx, rs = g.generate_checksum(T)
