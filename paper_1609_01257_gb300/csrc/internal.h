@@ -22,6 +22,10 @@ constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
 // thread only).
 const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded = false,
                            uint32_t out = 0);
+// Row kernel that stages each row in shared memory and stores it in
+// line-aligned pieces (for rows that do not start on 128-byte lines); 1, 2,
+// 4, 6 or 8 values per thread, 256-thread blocks.
+const void *rows_staged_kernel_fn(uint32_t vpt, bool banded, uint32_t out);
 const void *checksum_kernel_fn(uint32_t vpt, bool banded = false, uint32_t out = 0);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *batch_work_kernel_fn(uint32_t vpt);
@@ -63,7 +67,8 @@ struct LaunchShape {
   uint32_t vpt;
   uint32_t block;
   uint32_t grid;
-  uint32_t width;  // widest store in values (1, 2, 4) the shape may use
+  uint32_t width;       // widest store in values (1, 2, 4) the shape may use
+  bool staged = false;  // rows off the 128-byte lines: the staged row kernel
 };
 
 // Values-per-thread counts the row kernel is compiled for (256-thread

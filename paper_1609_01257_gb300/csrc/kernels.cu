@@ -274,6 +274,37 @@ __global__ void __launch_bounds__(BLOCK) rows_kernel(const RowsLaunch a) {
   }
 }
 
+// Row kernel for outputs whose rows do not start on 128-byte lines (a stream
+// count that is not a multiple of 16, or an output that does not start on a
+// line): the same work units (tiles, or (tile, band) units when banded), one
+// thread per stream slot of the tile, each row staged in shared memory and
+// stored in line-aligned pieces (emit_rows_staged).
+template <int VPT, bool BANDED, int OUT = 0>
+__global__ void __launch_bounds__(kBlock) rows_staged_kernel(const RowsLaunch a) {
+  __shared__ uint64_t stage[staged_words<VPT>()];
+  const uint64_t span = a.s_end - a.s_begin;
+  constexpr uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
+  const uint64_t band_rows = BANDED ? a.band_rows : a.rows;
+  const uint64_t n_bands = BANDED ? (a.rows + band_rows - 1) / band_rows : 1;
+  for (uint64_t w = blockIdx.x; w < n_tiles * n_bands; w += gridDim.x) {
+    const uint64_t tile = w % n_tiles;
+    const uint64_t band = BANDED ? w / n_tiles : 0;
+    const uint64_t rel0 = tile * tile_vals;
+    uint64_t st[VPT];
+    load_tile<VPT, 1>(st, a, rel0, span);
+    if constexpr (BANDED) {
+      __shared__ uint64_t jtab[16][16];
+      if (band) jump_states<VPT>(st, a.jump, band, jtab);  // band is the same for the whole block
+    }
+    const uint64_t r0 = band * band_rows;
+    const uint64_t rows = BANDED ? (a.rows - r0 < band_rows ? a.rows - r0 : band_rows) : a.rows;
+    emit_rows_staged<VPT, OUT>(st, a.out + r0 * a.pitch + rel0, a.pitch, rows, span - rel0, stage);
+    if (a.write_state && band == n_bands - 1)
+      store_tile_state<VPT, 1>(st, BANDED ? a.state_out : a.state, a, rel0, span);
+  }
+}
+
 // Separate init kernel (Listing S4): state[s] = initial state of id_base + s.
 __global__ void init_kernel(uint64_t *__restrict__ state, uint64_t n, uint64_t id_base,
                             uint32_t key) {
@@ -697,11 +728,28 @@ const void *select_batch(uint32_t vpt) {
 
 // Kernel entry points for the host-side launch code (launch.cpp); nullptr
 // when a shape is not compiled.
+template <bool BANDED, int OUT>
+const void *select_rows_staged_t(uint32_t vpt) {
+  switch (vpt) {
+    case 1: return reinterpret_cast<const void *>(&rows_staged_kernel<1, BANDED, OUT>);
+    case 2: return reinterpret_cast<const void *>(&rows_staged_kernel<2, BANDED, OUT>);
+    case 4: return reinterpret_cast<const void *>(&rows_staged_kernel<4, BANDED, OUT>);
+    case 6: return reinterpret_cast<const void *>(&rows_staged_kernel<6, BANDED, OUT>);
+    case 8: return reinterpret_cast<const void *>(&rows_staged_kernel<8, BANDED, OUT>);
+    default: return nullptr;
+  }
+}
+
 const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded, uint32_t out) {
   if (out == 1) return block == kBlock ? select_rows_star(vpt, width, banded) : nullptr;
   if (out != 0) return nullptr;
   if (banded) return block == kBlock ? select_rows_banded(vpt, width) : nullptr;
   return select_rows(vpt, width, policy, block);
+}
+const void *rows_staged_kernel_fn(uint32_t vpt, bool banded, uint32_t out) {
+  if (out == 1) return banded ? select_rows_staged_t<true, 1>(vpt) : select_rows_staged_t<false, 1>(vpt);
+  if (out != 0) return nullptr;
+  return banded ? select_rows_staged_t<true, 0>(vpt) : select_rows_staged_t<false, 0>(vpt);
 }
 const void *checksum_kernel_fn(uint32_t vpt, bool banded, uint32_t out) { return select_checksum(vpt, banded, out); }
 const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }

@@ -55,11 +55,42 @@ uint32_t default_vpt(uint64_t streams, int sms) {
   return 1;
 }
 
+// Values per thread of the staged row kernel for rows that do not start on
+// 128-byte lines (a stream count that is not a multiple of 16), or 0 to keep
+// the unstaged kernel.  Measured on GB300 (1024 rows, GB/s): 2^22 + 1
+// streams 6968 unstaged (24 per thread) vs 6882 staged at best, so from 3.5 M
+// streams the unstaged kernel stays; 3,000,017 streams 4411 unstaged vs 6762
+// staged at 8 per thread; 1,000,003 streams 4204 vs 6297 at 2; 250,001
+// streams 5642 at 4; 65,537 streams 4976 at 8 (banded).
+uint32_t staged_vpt(uint64_t streams, uint32_t requested, int sms) {
+  if (requested) return requested == 1 || requested == 2 || requested == 4 || requested == 6 || requested == 8
+                            ? requested : 0;
+  const uint64_t M = uint64_t(1) << 20;
+  if (streams >= 7 * M / 2) return 0;
+  if (streams >= 2 * M) return 8;
+  if (streams >= M / 2) return 2;
+  const uint64_t tiles8 = (streams + uint64_t(kGenBlock) * 8 - 1) / (uint64_t(kGenBlock) * 8);
+  return tiles8 * 2 < static_cast<uint64_t>(sms) ? 8 : 4;  // 8 when the launch will be banded
+}
+
 LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid,
                        uint32_t width, int policy) {
   LaunchShape sh;
   sh.block = block ? block : kGenBlock;
   const int sms = device_sm_count(device);
+  if (sh.block == kGenBlock && streams % 16 != 0) {
+    const uint32_t v = staged_vpt(streams, vpt, sms);
+    if (v) {
+      sh.staged = true;
+      sh.vpt = v;
+      sh.width = 1;
+      const uint64_t tiles = (streams + uint64_t(kGenBlock) * v - 1) / (uint64_t(kGenBlock) * v);
+      uint64_t grid = max_grid && max_grid < tiles ? max_grid : tiles;
+      if (grid > 0x7fffffffull) grid = 0x7fffffffull;
+      sh.grid = static_cast<uint32_t>(grid ? grid : 1);
+      return sh;
+    }
+  }
   if (vpt == 0) vpt = sh.block == kGenBlock ? default_vpt(streams, sms) : 8;
   sh.vpt = vpt;
   // One 8-byte store per value measured fastest once a thread holds six or
@@ -99,18 +130,30 @@ cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_po
       break;
     }
   if (width > static_cast<int>(sh.width)) width = static_cast<int>(sh.width);
-  const void *fn = rows_kernel_fn(sh.vpt, width, store_policy, sh.block, a.band_rows != 0, a.out_mode);
+  // Rows that do not start on 128-byte lines (a pitch that is not a multiple
+  // of 16 values, or an output off a line): a warp's run of 8-byte stores
+  // then touches nine 32-byte sectors instead of eight.  Shapes chosen for
+  // such rows (sh.staged), and shapes of 1-8 values per thread whose output
+  // starts off a line, run the staged row kernel, which stores line-aligned
+  // pieces; the tiles are the same.
+  const uint32_t vpt = sh.vpt;
+  const bool small_vpt = vpt == 1 || vpt == 2 || vpt == 4 || vpt == 6 || vpt == 8;
+  const bool staged = a.out && !a.ring_rows && sh.block == kGenBlock && small_vpt &&
+                      (sh.staged || a.pitch % 16 != 0 || base % 128 != 0);
+  const void *fn = staged ? rows_staged_kernel_fn(vpt, a.band_rows != 0, a.out_mode)
+                          : rows_kernel_fn(vpt, width, store_policy, sh.block, a.band_rows != 0, a.out_mode);
+  uint64_t grid = sh.grid;
+  const uint64_t span = a.s_end - a.s_begin;
   if (!fn) return cudaErrorInvalidValue;
   RowsLaunch args = a;
   void *params[] = {&args};
-  uint64_t grid = sh.grid;
   if (a.band_rows) {
     // One block per (tile, band) unit, unless the shape asked for fewer.
-    const uint64_t span = a.s_end - a.s_begin;
-    const uint64_t tiles = (span + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
+    const uint64_t tiles = (span + uint64_t(sh.block) * vpt - 1) / (uint64_t(sh.block) * vpt);
     const uint64_t units = tiles * ((a.rows + a.band_rows - 1) / a.band_rows);
     if (grid >= tiles) grid = units < 0x7fffffffull ? units : 0x7fffffffull;
   }
+  if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   cudaError_t e = cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(sh.block), params, 0, st);
   if (e == cudaSuccess) count_launch();
   return e;
@@ -220,8 +263,9 @@ uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh
   const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
   const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
   const uint64_t min_band = 128;
-  const void *fn = checksum ? checksum_kernel_fn(sh.vpt, true, out)
-                            : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true, out);
+  const void *fn = checksum    ? checksum_kernel_fn(sh.vpt, true, out)
+                   : sh.staged ? rows_staged_kernel_fn(sh.vpt, true, out)
+                               : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true, out);
   if (!fn || rows < 2 * min_band) return 0;  // no banded variant of this shape, or too few rows
   uint64_t target;
   if (checksum) {

@@ -121,19 +121,32 @@ class Generator:
         self._lib.rng_launch_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(g))
         return v.value, b.value, g.value
 
+    def _after_current(self):
+        # The library's work follows what torch's current stream has queued
+        # (e.g. the output's allocation) ...
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(self.device))
+        self.stream.wait_event(ev)
+
+    def _before_current(self):
+        # ... and torch's current stream waits for it, so that a tensor handed
+        # back is ready for whatever the caller queues next (``.cpu()``, ...).
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        torch.cuda.current_stream(self.device).wait_event(ev)
+
     def generate(self, iterations: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """Next ``iterations`` rows on the device (asynchronous on the
-        generator's compute stream)."""
+        """Next ``iterations`` rows on the device.  Asynchronous for the host:
+        the kernel runs on the generator's compute stream, and torch's current
+        stream is made to wait for it before the tensor is returned."""
         if out is None:
             out = torch.empty((iterations, self.streams), dtype=torch.uint64, device=self.device)
         assert out.is_cuda and out.is_contiguous() and out.element_size() == 8
         assert out.numel() >= iterations * self.streams
-        # Order the write after the tensor's allocation on torch's stream.
-        ev = torch.cuda.Event()
-        ev.record(torch.cuda.current_stream(self.device))
-        self.stream.wait_event(ev)
+        self._after_current()
         C.check(self._lib.rng_generate, self._h, iterations, ctypes.c_void_p(out.data_ptr()), None)
         out.record_stream(self.stream)
+        self._before_current()
         return out
 
     def generate_to(self, iterations: int, out_ptr: int):
@@ -145,12 +158,11 @@ class Generator:
         tensor), row ``i mod R`` for iteration ``i``; asynchronous."""
         assert ring.is_cuda and ring.is_contiguous() and ring.element_size() == 8
         assert ring.numel() % self.streams == 0 and ring.numel() >= self.streams
-        ev = torch.cuda.Event()
-        ev.record(torch.cuda.current_stream(self.device))
-        self.stream.wait_event(ev)
+        self._after_current()
         C.check(self._lib.rng_generate_ring, self._h, iterations, ctypes.c_void_p(ring.data_ptr()),
                 ring.numel() // self.streams)
         ring.record_stream(self.stream)
+        self._before_current()
         return ring
 
     def generate_to_host(self, iterations: int, out=None):
@@ -230,13 +242,12 @@ class Generator:
             row_xor = torch.empty(iterations, dtype=torch.uint64, device=self.device)
         if row_sum is None:
             row_sum = torch.empty(iterations, dtype=torch.uint64, device=self.device)
-        ev = torch.cuda.Event()
-        ev.record(torch.cuda.current_stream(self.device))
-        self.stream.wait_event(ev)
+        self._after_current()
         C.check(self._lib.rng_generate_checksum, self._h, iterations,
                 ctypes.c_void_p(row_xor.data_ptr()), ctypes.c_void_p(row_sum.data_ptr()))
         row_xor.record_stream(self.stream)
         row_sum.record_stream(self.stream)
+        self._before_current()
         return row_xor, row_sum
 
     def state(self) -> np.ndarray:

@@ -329,6 +329,21 @@ def test_few_streams_many_rows_split_into_bands(n, T):
     assert np.array_equal(b, want[T:])
 
 
+def test_generate_returns_a_tensor_ready_on_the_current_stream():
+    # generate() launches on the generator's own stream; the tensor it hands
+    # back must be readable at once on torch's current stream.  The memory is
+    # dirtied first (torch's allocator hands the same block back), so a read
+    # that ran ahead of the kernel would see the old values.
+    for T in (257, 300, 1000):
+        for _ in range(3):
+            junk = torch.full((T, 1), -1, dtype=torch.int64, device="cuda")
+            del junk
+            g = rng.Generator(1, 17)
+            got = g.generate(T).cpu().numpy()
+            g.close()
+            assert np.array_equal(got, oracle.generate(1, 17, T)), T
+
+
 @pytest.mark.parametrize("vpt", [24, 32, 64])
 def test_few_streams_many_rows_shapes_without_banded_variant(vpt):
     # Shapes compiled without a banded variant run unbanded.
