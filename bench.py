@@ -919,7 +919,13 @@ def sweep_leg(args, clocks=None):
     """Compact roofline sweep for the default line: at each stream count 2^16
     .. 2^28 (powers of 4), the library's default shape in full-write mode
     (4 GiB ring per launch, four launches) and in generate-and-checksum
-    mode (16 GiB worth of values)."""
+    mode (16 GiB worth of values).  Each full-write launch also reads and
+    writes every stream's state once (16 B per stream), which weighs as
+    much as the output at 2^28 streams (two rows per launch); the DRAM rate
+    including it is reported beside the output rate.  One call through the
+    ring would keep the states in registers, but then every block rewrites
+    its own few ring rows while its earlier stores still sit in L2, so L2
+    absorbs part of the output and the rate no longer measures HBM."""
     import torch
     sys.path.insert(0, ROOT)
     import paper_1609_01257_gb300 as rng
@@ -953,6 +959,7 @@ def sweep_leg(args, clocks=None):
         ck.close()
         points[f"2^{e}"] = {"rows_per_launch": rows, "values_per_thread": vpt,
                             "write_GBps": round(8 * n * rows * c / t / 1e9, 1),
+                            "dram_GBps_incl_state": round((8 * n * rows + 16 * n) * c / t / 1e9, 1),
                             "checksum_values_per_s": float(f"{n * T * cc / ct:.4g}")}
     t1 = time.time()
     del ring

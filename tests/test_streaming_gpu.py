@@ -115,6 +115,31 @@ def test_checksum_mode_largest_sweep_point():
         assert int(rx[i]) == gf2.apply(gf2.power(m, i), int(wx[0]))
 
 
+def test_ring_largest_sweep_point():
+    # Ring output at the sweep's largest stream count: 2^28 streams, 8
+    # iterations in one call through a ring of two 2 GiB rows (ring row j
+    # ends holding iteration 6 + j).  Both rows' XOR and sum against the
+    # oracle, sampled values one by one, then the next call continuing from
+    # the states the ring launch stored.
+    n, T, R, seed = 1 << 28, 8, 2, 1
+    g = rng.Generator(n, seed)
+    ring = torch.zeros((R, n), dtype=torch.int64, device="cuda").view(torch.uint64)
+    g.generate_ring(T, ring)
+    x9, s9 = g.generate_checksum(1)   # iteration 8, from the stored states
+    g.sync()
+    host = ring.cpu().numpy()
+    x9, s9 = x9.cpu().numpy(), s9.cpu().numpy()
+    del ring
+    g.close()
+    wx, ws, _ = oracle.row_checksums(n, seed, T + 1)
+    x, s = _row_checksums(host)
+    assert np.array_equal(x, wx[T - R:T]) and np.array_equal(s, ws[T - R:T])
+    assert int(x9[0]) == int(wx[T]) and int(s9[0]) == int(ws[T])
+    rs = np.random.default_rng(5)
+    for j, gg in zip(rs.integers(0, R, 16), rs.integers(0, n, 16)):
+        assert int(host[j, gg]) == oracle.value(int(gg), seed, T - R + int(j)), (j, gg)
+
+
 def test_device_resident_full_size_every_row():
     # The benchmark's device leg (2^22 x 1024 into device memory, default
     # shape): sampled values one by one, and every row's XOR and wrapping sum
