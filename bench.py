@@ -61,7 +61,6 @@ WORKLOADS = {
 CHECKSUM_ALU_OPS_PER_VALUE = {0: 10.6, 1: 10.5}
 NOMINAL_HBM_GBPS = 7900.0  # GB300 HBM3e, nominal
 METRIC = "GB/s of uint64 PRNG output (device and host-streamed) vs roofline; p50/p99 req latency"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "rows_kernel_traffic.md")
 
 
 def _dist():
@@ -86,11 +85,23 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(workload: str):
-    """DRAM bytes per launch of the row kernel from the committed ncu summary,
-    when it was taken on the current kernel source; else None."""
+PROFILES_DIR = os.path.join(ROOT, "profiles")
+
+# What the row-kernel launch ran (Generator.last_launch()["kernel"]).
+KERNEL_LABEL = {"register": "register stores (each thread stores its values)",
+                "staged": "rows staged in shared memory, stored as line-aligned 16-byte pieces",
+                "bulk": "rows staged in shared memory ({nb} buffers), written by TMA bulk copies (cp.async.bulk)"}
+KERNEL_FN = {"register": "rows_kernel", "staged": "rows_staged_kernel", "bulk": "rows_bulk_kernel"}
+STORE_POLICY_LABEL = {0: "default stores", 1: "streaming stores (st.global.cs); bulk copies where measured faster",
+                      2: "bulk copies for every device row"}
+
+
+def _traffic_per_launch(workload: str, kernel: str = "rows_kernel"):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary
+    (profiles/<kernel>_traffic.md), when it was taken on the current kernel
+    source; else None."""
     try:
-        txt = open(TRAFFIC_FILE).read()
+        txt = open(os.path.join(PROFILES_DIR, f"{kernel}_traffic.md")).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
@@ -358,7 +369,8 @@ def run_gpu(args, wl):
     k_count, k_total = gen.profile_stat("RNG_KERNEL")
     k_avg = max_over_ranks(k_total / max(k_count, 1))
     value = nbytes * ws * args.steps / dev_s / 1e9
-    vpt, block, grid = gen.launch_config()
+    ran = gen.last_launch()
+    vpt, block, grid = ran["values_per_thread"], ran["block"], ran["grid"]
     del out
     torch.cuda.empty_cache()
     # Denominators measured on this GPU, outside the timed regions.
@@ -507,7 +519,7 @@ def run_gpu(args, wl):
         return 0
 
     achieved = nbytes / k_avg / 1e9
-    traffic = _traffic_per_launch(args.workload)
+    traffic = _traffic_per_launch(args.workload, KERNEL_FN[ran["kernel"]])
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "values_per_s": value * 1e9 / 8, "n_gpus": ws,
         "steps": args.steps,
@@ -516,14 +528,15 @@ def run_gpu(args, wl):
         "config": {"workload": wl["name"] + _mode_label(args), "streams_per_gpu": n, "iterations": T,
                    "seed": seed, "output_mode": args.output_mode,
                    "bytes_per_step_per_gpu": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
-                   "stores": {"widest_values": args.store_width or "per shape",
-                              "policy": "streaming (st.global.cs)" if args.store_policy else "default"},
+                   "stores": {"kernel": KERNEL_LABEL[ran["kernel"]].format(nb=ran["row_buffers"]),
+                              "widest_values": args.store_width or "per shape",
+                              "policy": STORE_POLICY_LABEL.get(args.store_policy, str(args.store_policy))},
                    "l2": l2_note,
                    "parallelism": f"dp{ws} (disjoint stream-id blocks)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": f"{src}: hbm_gbs (copy, read+write) from MEASURED_PEAKS.json",
-                     "kernel": "rows_kernel", "kernel_avg_ms": k_avg * 1e3, "launches": k_count,
+                     "kernel": KERNEL_FN[ran["kernel"]], "kernel_avg_ms": k_avg * 1e3, "launches": k_count,
                      "write_ceiling_GBps": write_ceiling, "frac_write_ceiling": achieved / write_ceiling,
                      "write_ceiling_source": "measured here: torch fill_ over 2 GiB, best of 10",
                      "nominal_GBps": NOMINAL_HBM_GBPS, "frac_nominal": achieved / NOMINAL_HBM_GBPS},
@@ -896,13 +909,14 @@ def plain_leg(args, clocks=None, write_ceiling=None, peak=None):
     secs = timed_steps(torch, g.stream, step, steps, flush)
     t1 = time.time()
     c, kt = g.profile_stat("RNG_KERNEL")
-    vpt, block, grid = g.launch_config()
+    ran = g.last_launch()
+    vpt, block, grid = ran["values_per_thread"], ran["block"], ran["grid"]
     g.close()
     k_avg = kt / max(c, 1)
     nbytes = 8 * n * T
     d = {"config": {"workload": wl["name"], "streams": n, "iterations": T, "seed": seed,
                     "bytes_per_step": nbytes, "values_per_thread": vpt, "block": block, "grid": grid,
-                    "l2": flush.label()},
+                    "kernel": ran["kernel"], "l2": flush.label()},
          "value": nbytes * steps / secs / 1e9, "unit": "GB/s", "us_per_step": 1e6 * secs / steps,
          "kernel_us": 1e6 * k_avg, "kernel_GBps": nbytes / k_avg / 1e9, "steps": steps, "warmup": args.warmup}
     if write_ceiling:
@@ -944,7 +958,7 @@ def sweep_leg(args, clocks=None):
         for _ in range(4):
             g.generate_to(rows, ring.data_ptr())
         c, t = g.profile_stat("RNG_KERNEL")
-        vpt = g.launch_config()[0]
+        ran = g.last_launch()
         g.close()
         T = max(1, (16 * GIB) // (8 * n))
         ck = rng.Generator(n, 1, init=False)
@@ -957,7 +971,8 @@ def sweep_leg(args, clocks=None):
         ck.sync()
         cc, ct = ck.profile_stat("CHECKSUM_KERNEL")
         ck.close()
-        points[f"2^{e}"] = {"rows_per_launch": rows, "values_per_thread": vpt,
+        points[f"2^{e}"] = {"rows_per_launch": rows, "kernel": ran["kernel"],
+                            "values_per_thread": ran["values_per_thread"],
                             "write_GBps": round(8 * n * rows * c / t / 1e9, 1),
                             "dram_GBps_incl_state": round((8 * n * rows + 16 * n) * c / t / 1e9, 1),
                             "checksum_values_per_s": float(f"{n * T * cc / ct:.4g}")}
@@ -1194,7 +1209,8 @@ def run_sweep(args):
             for _ in range(launches):
                 g.generate_to(rows, out.data_ptr())
             c, t = g.profile_stat("RNG_KERNEL")
-            cfg = g.launch_config()
+            ran = g.last_launch()
+            cfg = (ran["values_per_thread"], ran["block"], ran["grid"], ran["kernel"])
             g.close()
             return 8 * n * rows * c / t / 1e9, (8 * n * rows + 16 * n) * c / t / 1e9, cfg
 
@@ -1236,7 +1252,7 @@ def run_sweep(args):
         _json_line({"sweep_streams": n, "rows_per_launch": rows, "launches": launches,
                     "write_GBps_by_vpt": {str(k): round(v, 1) for k, v in res.items()},
                     "dram_GBps_incl_state_by_vpt": {str(k): round(v, 1) for k, v in res_dram.items()},
-                    "default_shape": {"vpt": cfg[0], "grid": cfg[2], "GBps": round(dflt, 1),
+                    "default_shape": {"kernel": cfg[3], "vpt": cfg[0], "grid": cfg[2], "GBps": round(dflt, 1),
                                       "dram_GBps_incl_state": round(dflt_dram, 1)},
                     "checksum_iterations": T,
                     "checksum_values_per_s_by_vpt": {str(k): float(f"{v:.4g}") for k, v in ck_vps.items()},
@@ -1293,8 +1309,8 @@ def main(argv=None):
     ap.add_argument("--grid-blocks", type=int, default=0,
                     help="streaming/plain device leg: row-kernel grid (0 = one block per tile; fewer: "
                          "persistent blocks striding over the tiles)")
-    ap.add_argument("--store-policy", type=int, default=1, choices=[0, 1],
-                    help="streaming/plain device leg: 1 = streaming stores (st.global.cs), 0 = default stores")
+    ap.add_argument("--store-policy", type=int, default=1, choices=[0, 1, 2],
+                    help="streaming/plain device leg: 1 = streaming stores (st.global.cs), with bulk copies where measured faster; 0 = default stores; 2 = TMA bulk copies for every row")
     ap.add_argument("--iterations", type=int, default=0,
                     help="override the workload's iteration count (profiling captures of a smaller case)")
     args = ap.parse_args(argv)

@@ -93,7 +93,19 @@ typedef struct rng_opts {
     void *compute_stream;         /* cudaStream_t for kernels; NULL = own stream */
     int32_t device;               /* CUDA device ordinal; -1 = current device */
     uint32_t store_policy;        /* 0 = default stores, 1 (default) = streaming
-                                     stores (st.global.cs, evict-first) */
+                                     stores (st.global.cs, evict-first), with
+                                     the bulk-copy kernel where it measured
+                                     faster (device outputs of at least 128
+                                     rows per call) when the shape is left to
+                                     the library (values_per_thread,
+                                     block_threads, grid_blocks and
+                                     store_width all 0); 2 =
+                                     every device-output row staged in shared
+                                     memory and written by TMA bulk copies
+                                     (cp.async.bulk), 256-thread blocks, 0
+                                     (= 8), 4, 8 or 16 values per thread.
+                                     Host destinations always use register
+                                     stores */
     uint32_t host_wait_ms;        /* longest wait for a free staging slot while a
                                      host consumer holds them all; 0 = 600000 */
     uint32_t store_width;         /* widest store in values: 1, 2 or 4 (the
@@ -307,6 +319,25 @@ void *rng_compute_stream(rng_gen *g);
  * per block and blocks of the grid. */
 int rng_launch_config(const rng_gen *g, uint32_t *values_per_thread,
                       uint32_t *block_threads, uint32_t *grid_blocks);
+
+/* What the generator's last row-kernel launch ran (introspection; the paper
+ * has no counterpart).  kernel: RNG_KERNEL_REGISTER (each thread stores its
+ * values from registers), RNG_KERNEL_STAGED (rows staged in shared memory and
+ * stored as line-aligned 16-byte pieces) or RNG_KERNEL_BULK (rows staged in
+ * shared memory and written by TMA bulk copies, row_buffers buffers in turn).
+ * band_rows: rows per band of a banded launch, else 0.  Set info->struct_size
+ * = sizeof(rng_launch_info) first.  RNG_ESTATE before the first launch. */
+enum { RNG_KERNEL_REGISTER = 0, RNG_KERNEL_STAGED = 1, RNG_KERNEL_BULK = 2 };
+typedef struct rng_launch_info {
+    uint32_t struct_size;
+    uint32_t kernel;
+    uint32_t values_per_thread;
+    uint32_t block_threads;
+    uint32_t grid_blocks;
+    uint32_t row_buffers;
+    uint64_t band_rows;
+} rng_launch_info;
+int rng_last_launch(const rng_gen *g, rng_launch_info *info, rng_err **err);
 
 /* Releases the device state, buffers, streams and events.  NULL-safe. */
 void rng_destroy(rng_gen *g);

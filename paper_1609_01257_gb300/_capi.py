@@ -63,6 +63,14 @@ class RngHostStats(ctypes.Structure):
     ]
 
 
+class RngLaunchInfo(ctypes.Structure):
+    _fields_ = [("struct_size", c_u32), ("kernel", c_u32), ("values_per_thread", c_u32),
+                ("block_threads", c_u32), ("grid_blocks", c_u32), ("row_buffers", c_u32), ("band_rows", c_u64)]
+
+
+KERNEL_NAMES = {0: "register", 1: "staged", 2: "bulk"}
+
+
 class RngBatchOpts(ctypes.Structure):
     _fields_ = [
         ("struct_size", c_u32),
@@ -124,6 +132,7 @@ SIGNATURES = {
     "rng_sync": ([c_vp, P_err], c_int),
     "rng_compute_stream": ([c_vp], c_vp),
     "rng_launch_config": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)], c_int),
+    "rng_last_launch": ([c_vp, ctypes.POINTER(RngLaunchInfo), P_err], c_int),
     "rng_destroy": ([c_vp], None),
     "rng_prof_new": ([], c_vp),
     "rng_prof_add": ([c_vp, c_cp, c_cp, c_dbl, c_dbl], c_int),

@@ -57,6 +57,7 @@ struct rng_gen {
   rng_opts opts{};
   rngi::LaunchShape shape{};
   rngi::LaunchShape chunk_shape{};  // shape of the last streamed chunk width
+  rngi::LaunchInfo last_launch{};   // what the last row-kernel launch ran
   uint64_t chunk_span = 0;
   uint64_t *d_state = nullptr;
   uint64_t *d_state2 = nullptr;      // second state array for banded launches
@@ -179,11 +180,17 @@ int setup_bands(rng_gen *g, rngi::RowsLaunch &a, uint64_t br, bool *swap, rng_er
 // separate blocks: each band's blocks jump their states ahead over GF(2),
 // and the final states are written to the second state array, which then
 // becomes the current one.
-int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh, rng_err **err) {
+// device_out: a.out is device memory (the bulk-copy kernel may write it);
+// host destinations keep the register-store kernels.
+int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &shape, bool device_out,
+                    rng_err **err) {
   a.band_rows = 0;
   a.jump = nullptr;
   a.state_out = a.state;
   a.out_mode = g->opts.output_mode;
+  rngi::LaunchShape base = shape;
+  if (!device_out) base.bulk_lined = base.bulk_ragged = rngi::BulkChoice{};
+  const rngi::LaunchShape sh = rngi::resolve_shape(base, a);
   bool swap = false;
   if (!a.ring_rows && a.out && a.s_begin == 0 && a.s_end == g->n) {
     const uint64_t br = rngi::choose_band_rows(g->n, a.rows, sh, g->device, false, a.out_mode);
@@ -193,7 +200,7 @@ int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh
     }
   }
   long op = op_begin(g, "RNG_KERNEL", kQueueMain, g->compute);
-  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute);
+  cudaError_t st = rngi::launch_rows(a, sh, static_cast<int>(g->opts.store_policy), g->compute, &g->last_launch);
   op_end(g, op, g->compute);
   int rc = rngi::cuda_fail(err, st, "rows kernel launch");
   if (!rc && swap) std::swap(g->d_state, g->d_state2);
@@ -289,13 +296,17 @@ int launch_chunk(rng_gen *g, const Chunk &c, bool from_hash, uint64_t *dst, rng_
   a.from_hash = from_hash;
   a.write_state = 1;
   if (c.span != g->chunk_span) {
-    g->chunk_shape = rngi::rows_shape(c.span, g->opts.values_per_thread, g->opts.block_threads, g->device,
-                                      g->opts.grid_blocks, g->opts.store_width,
-                                      static_cast<int>(g->opts.store_policy));
+    // Chunks (which may be stored straight into host memory) run the
+    // register-store kernels, in the caller's shape unless that is a
+    // bulk-copy shape.
+    const bool bulk = g->opts.store_policy == rngi::kStoreBulk;
+    g->chunk_shape = rngi::rows_shape(c.span, bulk ? 0 : g->opts.values_per_thread, g->opts.block_threads,
+                                      g->device, g->opts.grid_blocks, g->opts.store_width,
+                                      bulk ? rngi::kStoreStreaming : static_cast<int>(g->opts.store_policy));
     g->chunk_span = c.span;
   }
   const rngi::LaunchShape sh = g->chunk_shape;
-  return gen_launch_rows(g, a, sh, err);
+  return gen_launch_rows(g, a, sh, false, err);
 }
 
 // What the host consumers do with each finished staging slot.
@@ -623,7 +634,7 @@ int direct_host(rng_gen *g, uint64_t T, uint64_t *dst, rng_err **err) {
   a.key = g->key;
   a.from_hash = !g->materialized;
   a.write_state = 1;
-  int rc = gen_launch_rows(g, a, g->shape, err);
+  int rc = gen_launch_rows(g, a, g->shape, false, err);
   if (rc) return rc;
   g->materialized = true;
   g->pos += T;
@@ -688,7 +699,13 @@ int rng_create(uint64_t streams, uint64_t seed, const rng_opts *opts, rng_gen **
   if (o.device_buffer_bytes == 0) o.device_buffer_bytes = size_t(32) << 20;
   if (o.device_buffer_bytes < 16 || o.device_buffer_bytes % 16)
     return rngi::fail(err, RNG_EINVAL, "rng_create: device_buffer_bytes must be a positive multiple of 16");
-  if (o.store_policy > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0 or 1");
+  if (o.store_policy > 2) return rngi::fail(err, RNG_EINVAL, "rng_create: store_policy must be 0, 1 or 2");
+  if (o.store_policy == 2 && ((o.block_threads && o.block_threads != rngi::kGenBlock) ||
+                              !(o.values_per_thread == 0 || o.values_per_thread == 4 ||
+                                o.values_per_thread == 8 || o.values_per_thread == 16)))
+    return rngi::fail(err, RNG_EINVAL,
+                      "rng_create: store_policy 2 (bulk copies) runs 256-thread blocks with 0, 4, 8 or 16 "
+                      "values per thread");
   if (o.host_path > 3) return rngi::fail(err, RNG_EINVAL, "rng_create: host_path must be 0, 1, 2 or 3");
   if (o.host_consumers > 64) return rngi::fail(err, RNG_EINVAL, "rng_create: host_consumers must be at most 64");
   if (o.output_mode > 1) return rngi::fail(err, RNG_EINVAL, "rng_create: output_mode must be 0 or 1");
@@ -820,7 +837,7 @@ int rng_generate(rng_gen *g, uint64_t iterations, uint64_t *out_dev, uint64_t *o
   a.key = g->key;
   a.from_hash = !g->materialized;
   a.write_state = 1;
-  rc = gen_launch_rows(g, a, g->shape, err);
+  rc = gen_launch_rows(g, a, g->shape, true, err);
   if (rc) return rc;
   g->materialized = true;
   g->pos += iterations;
@@ -849,7 +866,7 @@ int rng_generate_ring(rng_gen *g, uint64_t iterations, uint64_t *ring_dev, uint6
   a.from_hash = !g->materialized;
   a.write_state = 1;
   a.ring_rows = ring_rows;
-  rc = gen_launch_rows(g, a, g->shape, err);
+  rc = gen_launch_rows(g, a, g->shape, true, err);
   if (rc) return rc;
   g->materialized = true;
   g->pos += iterations;
@@ -1061,6 +1078,22 @@ int rng_launch_config(const rng_gen *g, uint32_t *vpt, uint32_t *block, uint32_t
   if (vpt) *vpt = g->shape.vpt;
   if (block) *block = g->shape.block;
   if (grid) *grid = g->shape.grid;
+  return RNG_OK;
+}
+
+int rng_last_launch(const rng_gen *g, rng_launch_info *info, rng_err **err) {
+  if (!g || !info) return rngi::fail(err, RNG_EINVAL, "rng_last_launch: NULL generator or info");
+  if (info->struct_size != sizeof(rng_launch_info))
+    return rngi::fail(err, RNG_EINVAL, "rng_last_launch: info.struct_size %u != %zu", info->struct_size,
+                      sizeof(rng_launch_info));
+  const rngi::LaunchInfo &l = g->last_launch;
+  if (l.block == 0) return rngi::fail(err, RNG_ESTATE, "rng_last_launch: no row-kernel launch yet");
+  info->kernel = l.kernel;
+  info->values_per_thread = l.vpt;
+  info->block_threads = l.block;
+  info->grid_blocks = l.grid;
+  info->row_buffers = l.row_buffers;
+  info->band_rows = l.band_rows;
   return RNG_OK;
 }
 

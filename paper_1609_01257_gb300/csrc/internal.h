@@ -13,6 +13,7 @@ namespace rngi {
 constexpr uint32_t kGenBlock = 256;  // threads per block of the generation kernels
 constexpr int kStoreDefault = 0;     // st.global
 constexpr int kStoreStreaming = 1;   // st.global.cs (evict-first)
+constexpr int kStoreBulk = 2;        // rows staged in shared memory, written by TMA bulk copies
 
 // Kernel entry points (kernels.cu); nullptr for shapes that are not compiled.
 // banded: the variant that splits rows into bands (few values per thread
@@ -26,6 +27,11 @@ const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, 
 // line-aligned pieces (for rows that do not start on 128-byte lines); 1, 2,
 // 4, 6 or 8 values per thread, 256-thread blocks.
 const void *rows_staged_kernel_fn(uint32_t vpt, bool banded, uint32_t out);
+// Row kernel whose rows are written by TMA bulk copies from `nb` shared
+// buffers (2 or 4 values per thread with 8 buffers, 8 with 4 or 8, 16 with
+// 4; 256-thread blocks), and its dynamic shared memory in bytes.
+const void *rows_bulk_kernel_fn(uint32_t vpt, uint32_t nb, bool banded, uint32_t out);
+size_t rows_bulk_smem_bytes(uint32_t vpt, uint32_t nb);
 const void *checksum_kernel_fn(uint32_t vpt, bool banded = false, uint32_t out = 0);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *batch_work_kernel_fn(uint32_t vpt);
@@ -63,12 +69,30 @@ struct RowsLaunch {
   uint32_t out_mode;    // value emitted per state: 0 the state, 1 xorshift64* (selects the kernel)
 };
 
+// Values per thread and row buffers of the bulk-copy row kernel (nb == 0:
+// not used).
+struct BulkChoice {
+  uint32_t vpt = 0;
+  uint32_t nb = 0;
+};
+
 struct LaunchShape {
   uint32_t vpt;
   uint32_t block;
   uint32_t grid;
-  uint32_t width;       // widest store in values (1, 2, 4) the shape may use
-  bool staged = false;  // rows off the 128-byte lines: the staged row kernel
+  uint32_t width;         // widest store in values (1, 2, 4) the shape may use
+  bool staged = false;    // rows off the 128-byte lines: the staged row kernel
+  BulkChoice bulk_lined;  // bulk-copy kernel for outputs whose rows start on 128-byte lines
+  BulkChoice bulk_ragged; // ... and for the others
+  bool bulk_always = false; // store_policy 2: bulk copies for every device row (else from 128 rows per launch)
+  uint32_t bulk_nb = 0;   // set by resolve_shape: this launch runs the bulk kernel (vpt values per thread)
+};
+
+// What one row-kernel launch ran (rng_launch_info without struct_size).
+struct LaunchInfo {
+  uint32_t kernel = 0;
+  uint32_t vpt = 0, block = 0, grid = 0, row_buffers = 0;
+  uint64_t band_rows = 0;
 };
 
 // Values-per-thread counts the row kernel is compiled for (256-thread
@@ -80,9 +104,15 @@ bool rows_shape_supported(uint32_t vpt, uint32_t block);
 // stride over tiles).  `policy` names the variant that will run.
 LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid = 0,
                        uint32_t width = 0, int policy = 1);
-// store_policy: 0 default, 1 streaming (.cs).  Stores are the widest of
-// sh.width and what the output's alignment allows.
-cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st);
+// The shape one launch with output a.out runs: the bulk-copy kernel when
+// the shape names one for the alignment of a.out's rows (device outputs
+// only: the caller passes no host destination here), else `sh` as chosen.
+LaunchShape resolve_shape(const LaunchShape &sh, const RowsLaunch &a);
+// store_policy: 0 default, 1 streaming (.cs), 2 bulk copies.  Register
+// stores are the widest of sh.width and what the output's alignment allows.
+// `sh` must come from resolve_shape.  info (optional) receives what ran.
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st,
+                        LaunchInfo *info = nullptr);
 cudaError_t launch_init(uint64_t *state, uint64_t n, uint64_t id_base, uint32_t key,
                         cudaStream_t st);
 // n words from device memory `src` to page-locked host memory `dst` (a

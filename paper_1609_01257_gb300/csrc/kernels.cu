@@ -179,6 +179,92 @@ __device__ __forceinline__ void emit_rows_staged(uint64_t (&st)[VPT], uint64_t *
   __syncthreads();  // the buffers are free for the next tile or unit
 }
 
+// TMA bulk copies (cp.async.bulk, shared::cta -> global) ---------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Orders this thread's earlier shared-memory writes before later copies of
+// the async proxy (the bulk copies read shared memory through it).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// `bytes` (a multiple of 16) from shared `src` to global `dst`, both 16-byte
+// aligned, as part of the issuing thread's current bulk group.
+__device__ __forceinline__ void bulk_store(uint64_t *dst, const uint64_t *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until at most N of this thread's committed groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// Waits until all of this thread's groups are complete (their writes done).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Shared words of the bulk row kernel: NB row buffers of one tile plus two
+// words (a row whose segment starts on an odd word is staged one word
+// further on, so that its 16-byte-aligned body is 16-byte aligned in shared
+// memory too).
+template <int VPT, int NB>
+__host__ __device__ constexpr int bulk_words() {
+  return NB * (kBlock * VPT + 2);
+}
+
+// Rows of one tile written by the TMA unit: each row's values go to one of
+// NB shared buffers (used in turn: `kb` is the next buffer and `warm` the
+// rows this block has staged, up to NB; both continue across the block's
+// tiles), one barrier per row, then one thread
+// issues a bulk copy of the row segment's 16-byte-aligned body and plain
+// 8-byte stores of an odd head or tail.  The SMs' store path then carries
+// only shared-memory writes.  A buffer is refilled only after the copy that
+// read it NB rows earlier has finished reading.  Values past `span` are
+// staged but not copied.  ring != 0: rows wrap around a ring of `ring` rows.
+// Every thread of the block must call it; the issuing thread must wait for
+// its groups (bulk_wait_all) before the block exits.
+template <int VPT, int NB, int OUT = 0>
+__device__ __forceinline__ void emit_rows_bulk(uint64_t (&st)[VPT], uint64_t *row, uint64_t pitch, uint64_t rows,
+                                               uint64_t span, uint64_t ring, uint64_t *buf, uint32_t &kb,
+                                               uint32_t &warm) {
+  static_assert(NB >= 2, "NB: at least 2");
+  constexpr int kTile = kBlock * VPT;
+  constexpr int kBuf = kTile + 2;
+  const int n = span < static_cast<uint64_t>(kTile) ? static_cast<int>(span) : kTile;
+  uint64_t *const first = row;
+  uint64_t in_ring = 0;
+  for (uint64_t r = 0; r < rows; ++r) {
+    const int p = static_cast<int>((reinterpret_cast<uintptr_t>(row) >> 3) & 1);  // segment starts on an odd word
+    uint64_t *b = buf + kb * kBuf;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) b[p + threadIdx.x + kBlock * j] = prng::emitted<OUT>(st[j]);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) st[v] = prng::xorshift_update(st[v]);
+    fence_proxy_async_smem();
+    // After this barrier the block fills the next buffer, last read by the
+    // copy issued NB - 1 rows before this one: at most NB - 2 later copies
+    // may still be reading.
+    if (threadIdx.x == 0 && warm + 1 >= NB) bulk_wait_read<NB - 2>();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int body = (n - p) & ~1;
+      if (p) store_one<kPolicyStreaming>(row, b[1]);
+      if ((n - p) & 1) store_one<kPolicyStreaming>(row + n - 1, b[p + n - 1]);
+      if (body > 0) bulk_store(row + p, b + 2 * p, 8u * static_cast<uint32_t>(body));
+      bulk_commit();
+    }
+    kb = kb + 1 == NB ? 0 : kb + 1;
+    if (warm < NB) ++warm;
+    row += pitch;
+    if (ring && ++in_ring == ring) {
+      row = first;
+      in_ring = 0;
+    }
+  }
+}
+
 // Whether every row of a segment starting at `row0` with pitch `pitch` starts
 // on a 128-byte line.
 __device__ __forceinline__ bool rows_line_aligned(const uint64_t *row0, uint64_t pitch) {
@@ -303,6 +389,39 @@ __global__ void __launch_bounds__(kBlock) rows_staged_kernel(const RowsLaunch a)
     if (a.write_state && band == n_bands - 1)
       store_tile_state<VPT, 1>(st, BANDED ? a.state_out : a.state, a, rel0, span);
   }
+}
+
+// Row kernel whose rows are written by TMA bulk copies from shared memory
+// (emit_rows_bulk): the same work units as rows_staged_kernel, any row
+// alignment, and rings when unbanded.  The dynamic shared memory holds the
+// NB row buffers (bulk_words<VPT, NB>() words).
+template <int VPT, int NB, bool BANDED, int OUT = 0>
+__global__ void __launch_bounds__(kBlock) rows_bulk_kernel(const RowsLaunch a) {
+  extern __shared__ __align__(128) uint64_t bulk_buf[];
+  const uint64_t span = a.s_end - a.s_begin;
+  constexpr uint64_t tile_vals = static_cast<uint64_t>(kBlock) * VPT;
+  const uint64_t n_tiles = (span + tile_vals - 1) / tile_vals;
+  const uint64_t band_rows = BANDED ? a.band_rows : a.rows;
+  const uint64_t n_bands = BANDED ? (a.rows + band_rows - 1) / band_rows : 1;
+  uint32_t kb = 0, warm = 0;
+  for (uint64_t w = blockIdx.x; w < n_tiles * n_bands; w += gridDim.x) {
+    const uint64_t tile = w % n_tiles;
+    const uint64_t band = BANDED ? w / n_tiles : 0;
+    const uint64_t rel0 = tile * tile_vals;
+    uint64_t st[VPT];
+    load_tile<VPT, 1>(st, a, rel0, span);
+    if constexpr (BANDED) {
+      __shared__ uint64_t jtab[16][16];
+      if (band) jump_states<VPT>(st, a.jump, band, jtab);  // band is the same for the whole block
+    }
+    const uint64_t r0 = band * band_rows;
+    const uint64_t rows = BANDED ? (a.rows - r0 < band_rows ? a.rows - r0 : band_rows) : a.rows;
+    emit_rows_bulk<VPT, NB, OUT>(st, a.out + r0 * a.pitch + rel0, a.pitch, rows, span - rel0,
+                                 BANDED ? 0 : a.ring_rows, bulk_buf, kb, warm);
+    if (a.write_state && band == n_bands - 1)
+      store_tile_state<VPT, 1>(st, BANDED ? a.state_out : a.state, a, rel0, span);
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
 }
 
 // Separate init kernel (Listing S4): state[s] = initial state of id_base + s.
@@ -738,6 +857,24 @@ const void *select_rows_staged_t(uint32_t vpt) {
     case 8: return reinterpret_cast<const void *>(&rows_staged_kernel<8, BANDED, OUT>);
     default: return nullptr;
   }
+}
+
+template <bool BANDED, int OUT>
+const void *select_rows_bulk_t(uint32_t vpt, uint32_t nb) {
+  if (vpt == 4 && nb == 8) return reinterpret_cast<const void *>(&rows_bulk_kernel<4, 8, BANDED, OUT>);
+  if (vpt == 8 && nb == 12) return reinterpret_cast<const void *>(&rows_bulk_kernel<8, 12, BANDED, OUT>);
+  if (vpt == 16 && nb == 4) return reinterpret_cast<const void *>(&rows_bulk_kernel<16, 4, BANDED, OUT>);
+  return nullptr;
+}
+
+const void *rows_bulk_kernel_fn(uint32_t vpt, uint32_t nb, bool banded, uint32_t out) {
+  if (out == 1) return banded ? select_rows_bulk_t<true, 1>(vpt, nb) : select_rows_bulk_t<false, 1>(vpt, nb);
+  if (out != 0) return nullptr;
+  return banded ? select_rows_bulk_t<true, 0>(vpt, nb) : select_rows_bulk_t<false, 0>(vpt, nb);
+}
+
+size_t rows_bulk_smem_bytes(uint32_t vpt, uint32_t nb) {
+  return size_t(nb) * (size_t(kBlock) * vpt + 2) * sizeof(uint64_t);
 }
 
 const void *rows_kernel_fn(uint32_t vpt, int width, int policy, uint32_t block, bool banded, uint32_t out) {

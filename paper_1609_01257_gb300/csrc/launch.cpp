@@ -73,11 +73,63 @@ uint32_t staged_vpt(uint64_t streams, uint32_t requested, int sms) {
   return tiles8 * 2 < static_cast<uint64_t>(sms) ? 8 : 4;  // 8 when the launch will be banded
 }
 
+// Row buffers of the bulk-copy row kernel for `vpt` values per thread (0 if
+// that count has no bulk variant).
+uint32_t bulk_buffers(uint32_t vpt) {
+  switch (vpt) {
+    case 4: return 8;
+    case 8: return 12;
+    case 16: return 4;
+    default: return 0;
+  }
+}
+
+// Bulk-copy row kernel (values per thread, row buffers) chosen when the
+// caller leaves the shape to the library, for rows on 128-byte lines
+// (`lined`) and off them.  Measured on GB300 (1024 rows, GB/s; the register-
+// store or staged kernel in brackets):
+//  - on the lines: 2^22 streams 7517 at (8, 12) [7470]; below 3.5 M streams
+//    the register kernels stay ahead (2^20: 7211 [7247]; 2^16: 6574 [6858]);
+//  - off the lines at (8, 12): 2^22 + 1 streams 7125 [6957], an output one
+//    word off a line 7147 [6893], 3,000,017 streams 6983 [6713], 250,001
+//    7078 [5629], 65,537 (banded) 6343 [4957]; at (16, 4): 1,000,003
+//    streams 6769 [6333] (6565 at (8, 12)).
+// Each copy has a fixed cost: 4 KiB copies (two values per thread) stayed
+// near 4.2 TB/s, so bulk tiles hold 8 KiB and more.  With one block per SM
+// (the buffers take most of its shared memory) each tile's start -- loading
+// its states -- is exposed, so launches of few rows keep the register
+// kernels: 2^22 streams x 128 rows 7221 [7209], 2^24 x 32 rows 6574 [6580],
+// 2^26 x 8 rows 4852 [5368], 2^28 x 2 rows 2233 [3503].
+constexpr uint64_t kBulkMinRows = 128;
+BulkChoice bulk_default(uint64_t streams, bool lined) {
+  const uint64_t M = uint64_t(1) << 20;
+  if (lined) return streams >= 7 * M / 2 ? BulkChoice{8, 12} : BulkChoice{};
+  if (streams < 64 * 1024) return BulkChoice{};
+  if (streams >= M / 2 && streams < 2 * M) return BulkChoice{16, 4};
+  return BulkChoice{8, 12};
+}
+
 LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int device, uint32_t max_grid,
                        uint32_t width, int policy) {
   LaunchShape sh;
   sh.block = block ? block : kGenBlock;
   const int sms = device_sm_count(device);
+  if (policy == kStoreBulk) {
+    // Every row written by bulk copies, whatever its alignment.
+    sh.vpt = vpt ? vpt : 8;
+    sh.bulk_lined = sh.bulk_ragged = BulkChoice{sh.vpt, bulk_buffers(sh.vpt)};
+    sh.bulk_always = true;
+    sh.width = 1;
+    const uint64_t tiles = (streams + uint64_t(kGenBlock) * sh.vpt - 1) / (uint64_t(kGenBlock) * sh.vpt);
+    uint64_t grid = max_grid && max_grid < tiles ? max_grid : tiles;
+    if (grid > 0x7fffffffull) grid = 0x7fffffffull;
+    sh.grid = sh.bulk_lined.nb && sh.block == kGenBlock ? static_cast<uint32_t>(grid ? grid : 1) : 0;
+    return sh;
+  }
+  if (policy == kStoreStreaming && vpt == 0 && sh.block == kGenBlock && max_grid == 0 && width == 0) {
+    sh.bulk_lined = bulk_default(streams, true);
+    sh.bulk_ragged = bulk_default(streams, false);
+  }
   if (sh.block == kGenBlock && streams % 16 != 0) {
     const uint32_t v = staged_vpt(streams, vpt, sms);
     if (v) {
@@ -117,7 +169,28 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
   return sh;
 }
 
-cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st) {
+LaunchShape resolve_shape(const LaunchShape &sh, const RowsLaunch &a) {
+  LaunchShape r = sh;
+  r.bulk_nb = 0;
+  if (!a.out) return r;
+  const bool lined = a.pitch % 16 == 0 && reinterpret_cast<uintptr_t>(a.out) % 128 == 0;
+  const BulkChoice c = lined ? sh.bulk_lined : sh.bulk_ragged;
+  if (!c.nb || (!sh.bulk_always && a.rows < kBulkMinRows)) return r;
+  r.vpt = c.vpt;
+  r.bulk_nb = c.nb;
+  r.staged = false;
+  r.width = 1;
+  const uint64_t span = a.s_end - a.s_begin;
+  const uint64_t tiles = (span + uint64_t(kGenBlock) * c.vpt - 1) / (uint64_t(kGenBlock) * c.vpt);
+  uint64_t grid = tiles;
+  if (sh.vpt == c.vpt && sh.grid && sh.grid < tiles) grid = sh.grid;  // a grid the caller asked for
+  if (grid > 0x7fffffffull) grid = 0x7fffffffull;
+  r.grid = static_cast<uint32_t>(grid ? grid : 1);
+  return r;
+}
+
+cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_policy, cudaStream_t st,
+                        LaunchInfo *info) {
   if (a.band_rows && (a.ring_rows || !a.jump || (a.write_state && a.state_out == a.state)))
     return cudaErrorInvalidValue;
   // Widest store the output's alignment allows: every row must start on an
@@ -138,13 +211,22 @@ cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_po
   // pieces; the tiles are the same.
   const uint32_t vpt = sh.vpt;
   const bool small_vpt = vpt == 1 || vpt == 2 || vpt == 4 || vpt == 6 || vpt == 8;
-  const bool staged = a.out && !a.ring_rows && sh.block == kGenBlock && small_vpt &&
+  const bool bulk = a.out && sh.bulk_nb;
+  const bool staged = !bulk && a.out && !a.ring_rows && sh.block == kGenBlock && small_vpt &&
                       (sh.staged || a.pitch % 16 != 0 || base % 128 != 0);
-  const void *fn = staged ? rows_staged_kernel_fn(vpt, a.band_rows != 0, a.out_mode)
-                          : rows_kernel_fn(vpt, width, store_policy, sh.block, a.band_rows != 0, a.out_mode);
+  const int policy = store_policy == kStoreBulk ? kStoreStreaming : store_policy;
+  const void *fn = bulk     ? rows_bulk_kernel_fn(vpt, sh.bulk_nb, a.band_rows != 0, a.out_mode)
+                   : staged ? rows_staged_kernel_fn(vpt, a.band_rows != 0, a.out_mode)
+                            : rows_kernel_fn(vpt, width, policy, sh.block, a.band_rows != 0, a.out_mode);
   uint64_t grid = sh.grid;
   const uint64_t span = a.s_end - a.s_begin;
   if (!fn) return cudaErrorInvalidValue;
+  size_t smem = 0;
+  if (bulk) {
+    smem = rows_bulk_smem_bytes(vpt, sh.bulk_nb);
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
   RowsLaunch args = a;
   void *params[] = {&args};
   if (a.band_rows) {
@@ -154,8 +236,18 @@ cudaError_t launch_rows(const RowsLaunch &a, const LaunchShape &sh, int store_po
     if (grid >= tiles) grid = units < 0x7fffffffull ? units : 0x7fffffffull;
   }
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
-  cudaError_t e = cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(sh.block), params, 0, st);
-  if (e == cudaSuccess) count_launch();
+  cudaError_t e = cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(sh.block), params, smem, st);
+  if (e == cudaSuccess) {
+    count_launch();
+    if (info) {
+      info->kernel = bulk ? RNG_KERNEL_BULK : staged ? RNG_KERNEL_STAGED : RNG_KERNEL_REGISTER;
+      info->vpt = vpt;
+      info->block = sh.block;
+      info->grid = static_cast<uint32_t>(grid);
+      info->row_buffers = bulk ? sh.bulk_nb : 0;
+      info->band_rows = a.band_rows;
+    }
+  }
   return e;
 }
 
@@ -263,9 +355,10 @@ uint64_t choose_band_rows(uint64_t streams, uint64_t rows, const LaunchShape &sh
   const uint64_t sms = static_cast<uint64_t>(device_sm_count(device));
   const uint64_t tiles = (streams + uint64_t(sh.block) * sh.vpt - 1) / (uint64_t(sh.block) * sh.vpt);
   const uint64_t min_band = 128;
-  const void *fn = checksum    ? checksum_kernel_fn(sh.vpt, true, out)
-                   : sh.staged ? rows_staged_kernel_fn(sh.vpt, true, out)
-                               : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true, out);
+  const void *fn = checksum     ? checksum_kernel_fn(sh.vpt, true, out)
+                   : sh.bulk_nb ? rows_bulk_kernel_fn(sh.vpt, sh.bulk_nb, true, out)
+                   : sh.staged  ? rows_staged_kernel_fn(sh.vpt, true, out)
+                                : rows_kernel_fn(sh.vpt, 1, kStoreStreaming, sh.block, true, out);
   if (!fn || rows < 2 * min_band) return 0;  // no banded variant of this shape, or too few rows
   uint64_t target;
   if (checksum) {

@@ -121,6 +121,17 @@ class Generator:
         self._lib.rng_launch_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(g))
         return v.value, b.value, g.value
 
+    def last_launch(self) -> dict:
+        """What the last row-kernel launch ran: kernel ("register", "staged"
+        or "bulk"), values per thread, block, grid, bulk row buffers and band
+        rows (0 = unbanded)."""
+        info = C.RngLaunchInfo()
+        info.struct_size = ctypes.sizeof(C.RngLaunchInfo)
+        C.check(self._lib.rng_last_launch, self._h, ctypes.byref(info))
+        return {"kernel": C.KERNEL_NAMES.get(info.kernel, str(info.kernel)),
+                "values_per_thread": info.values_per_thread, "block": info.block_threads,
+                "grid": info.grid_blocks, "row_buffers": info.row_buffers, "band_rows": info.band_rows}
+
     def _after_current(self):
         # The library's work follows what torch's current stream has queued
         # (e.g. the output's allocation) ...

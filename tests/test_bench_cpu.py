@@ -30,14 +30,21 @@ def test_clock_samples_inside_the_timed_region():
 
 
 def test_traffic_lookup_tracks_kernel_sources(tmp_path, monkeypatch):
-    f = tmp_path / "t.md"
+    f = tmp_path / "rows_bulk_kernel_traffic.md"
     f.write_text(f"kernel_source_sha256_16: {bench._kernel_source_hash()}\n"
                  "traffic_bytes_per_launch[streaming]: 3.5e+10\n")
-    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
-    assert bench._traffic_per_launch("streaming") == 3.5e10
-    assert bench._traffic_per_launch("plain") is None
+    monkeypatch.setattr(bench, "PROFILES_DIR", str(tmp_path))
+    assert bench._traffic_per_launch("streaming", "rows_bulk_kernel") == 3.5e10
+    assert bench._traffic_per_launch("plain", "rows_bulk_kernel") is None
+    assert bench._traffic_per_launch("streaming", "rows_kernel") is None  # no summary for that kernel
     f.write_text("kernel_source_sha256_16: 0000000000000000\ntraffic_bytes_per_launch[streaming]: 3.5e+10\n")
-    assert bench._traffic_per_launch("streaming") is None
+    assert bench._traffic_per_launch("streaming", "rows_bulk_kernel") is None
+
+
+def test_committed_traffic_summary_matches_the_kernel_sources():
+    # The streaming workload's device leg runs the bulk-copy row kernel; its
+    # committed ncu summary must be taken on the current kernel sources.
+    assert bench._traffic_per_launch("streaming", "rows_bulk_kernel") is not None
 
 
 class _FakeEvent:

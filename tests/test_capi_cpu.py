@@ -250,7 +250,7 @@ def test_batch_and_server_options_are_checked_on_the_host(L):
 
 @pytest.mark.parametrize("field,bad", [
     ("values_per_thread", 9), ("block_threads", 384), ("device_buffer_bytes", 24), ("device_buffer_bytes", 8),
-    ("store_policy", 2), ("host_path", 4), ("host_consumers", 65), ("output_mode", 2), ("store_width", 3),
+    ("store_policy", 3), ("host_path", 4), ("host_consumers", 65), ("output_mode", 2), ("store_width", 3),
     ("stream_offset", (1 << 32) - 15),
 ])
 def test_generator_options_are_checked_on_the_host(L, field, bad):
@@ -275,6 +275,26 @@ def test_alternative_output_mode_shapes_are_checked_on_the_host(L):
     for vpt, block in [(6, 0), (12, 0), (8, 128)]:
         o.values_per_thread, o.block_threads = vpt, block
         assert L.rng_create(4096, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL, (vpt, block)
+
+
+def test_bulk_copy_shapes_are_checked_on_the_host(L):
+    # store_policy 2 (rows written by TMA bulk copies) is compiled for
+    # 256-thread blocks with 4, 8 or 16 values per thread.
+    o = C.RngOpts()
+    L.rng_opts_default(ctypes.byref(o))
+    o.store_policy = 2
+    h = ctypes.c_void_p()
+    for vpt, block in [(1, 0), (2, 0), (6, 0), (24, 0), (8, 128), (8, 512)]:
+        o.values_per_thread, o.block_threads = vpt, block
+        assert L.rng_create(4096, 1, ctypes.byref(o), ctypes.byref(h), None) == C.RNG_EINVAL, (vpt, block)
+    assert not h
+
+
+def test_last_launch_rejects_bad_arguments_without_a_gpu(L):
+    info = C.RngLaunchInfo()
+    info.struct_size = ctypes.sizeof(C.RngLaunchInfo)
+    assert L.rng_last_launch(None, ctypes.byref(info), None) == C.RNG_EINVAL
+    assert ctypes.sizeof(C.RngLaunchInfo) == 32
 
 
 def test_host_alloc_rejects_bad_arguments_without_a_gpu(L):
