@@ -1276,8 +1276,8 @@ def main(argv=None):
     ap.add_argument("--batch-mode", type=int, default=0, help="batched: 0 autotune, 1 per block, 2 persistent")
     ap.add_argument("--step-bytes", type=int, default=2 << 30, help="served: output bytes per step")
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
-    ap.add_argument("--server-vpt", type=int, default=8, help="served: values per thread")
-    ap.add_argument("--server-mode", type=int, default=2, help="served: 1 one unit per block, 2 persistent")
+    ap.add_argument("--server-vpt", type=int, default=4, help="served: values per thread")
+    ap.add_argument("--server-mode", type=int, default=1, help="served: 1 one unit per block, 2 persistent")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64])
     ap.add_argument("--sweep-checksum-vpts", type=int, nargs="+", default=[1, 2, 4, 8, 16, 32, 64])
     ap.add_argument("--skip-streams", type=int, nargs="+", default=[1 << 22, 1 << 26, 1 << 28],

@@ -538,14 +538,19 @@ typedef struct rng_server_opts {
     uint64_t hbm_budget_bytes;    /* device arena for outputs and states; default 64 GiB */
     uint64_t step_bytes;          /* output bytes one step aims to produce; default 2 GiB */
     uint32_t max_steps_in_flight; /* launched, unfinished steps; default 2 */
-    uint32_t values_per_thread;   /* 1..32 (power of two); 0 = 8 */
+    uint32_t values_per_thread;   /* 1, 2, 4, 6, 8, 12, 16, 24 or 32; 0 = 4 */
     uint32_t max_units_per_step;  /* work-table capacity per step; default 1<<20 */
     int32_t device;               /* -1 = current */
     void *stream;                 /* cudaStream_t; NULL = own stream */
-    uint32_t mode;                /* 1 = one work unit per block, 2 (default) =
-                                     persistent blocks with a counter (equal
-                                     within noise in 15 s runs: p99 1.58 vs
-                                     1.50 ms) */
+    uint32_t mode;                /* 1 (default) = one work unit per block,
+                                     2 = persistent blocks with a counter.
+                                     The defaults (4 values per thread, one
+                                     unit per block) gave the lowest p99 over
+                                     20 s of the Poisson workload: 1.09 ms,
+                                     against 1.24 at 8 per thread with
+                                     persistent blocks: a step's kernel must
+                                     drain before the next one starts, and
+                                     smaller units shorten that tail */
 } rng_server_opts;
 
 typedef struct rng_server_stats {

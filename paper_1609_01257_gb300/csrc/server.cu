@@ -56,7 +56,8 @@ struct TableSlot {
   rngi::BatchInstance *h_inst = nullptr, *d_inst = nullptr;
   rngi::BatchUnit *h_units = nullptr, *d_units = nullptr;
   uint32_t *d_counter = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t uploaded = nullptr;  // the slot's tables are on the device
+  cudaEvent_t done = nullptr;      // the step using the slot has finished
 };
 
 struct Step {
@@ -117,6 +118,10 @@ struct rng_server {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // Table uploads and counter resets run here, ordered before their step's
+  // kernel by the slot's `uploaded` event, so that they overlap the step
+  // already running instead of queueing behind it on `stream`.
+  cudaStream_t upload = nullptr;
   uint8_t *base = nullptr;
   Arena arena;
   std::vector<TableSlot> slots;
@@ -190,14 +195,18 @@ struct rng_server {
     // Units stay in request order, each request's tiles together: blocks
     // running at the same time write neighbouring parts of one output (as in
     // the batched form, where this beat sorting all units by size).
+    // The slot is free, so no kernel reads its device tables any more and
+    // its last upload from the host tables has finished.
     cudaError_t e = cudaMemcpyAsync(ts.d_inst, ts.h_inst, n_inst * sizeof(rngi::BatchInstance),
-                                    cudaMemcpyHostToDevice, stream);
+                                    cudaMemcpyHostToDevice, upload);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ts.d_units, ts.h_units, n_units * sizeof(rngi::BatchUnit), cudaMemcpyHostToDevice, stream);
+      e = cudaMemcpyAsync(ts.d_units, ts.h_units, n_units * sizeof(rngi::BatchUnit), cudaMemcpyHostToDevice, upload);
     // Work distribution: one unit per block (hardware dispatch in table
     // order), or persistent blocks taking units from a counter.
     const bool per_block = opts.mode != 2;
-    if (e == cudaSuccess && !per_block) e = cudaMemsetAsync(ts.d_counter, 0, sizeof(uint32_t), stream);
+    if (e == cudaSuccess && !per_block) e = cudaMemsetAsync(ts.d_counter, 0, sizeof(uint32_t), upload);
+    if (e == cudaSuccess) e = cudaEventRecord(ts.uploaded, upload);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ts.uploaded, 0);
     const uint64_t resident = uint64_t(sms) * grid_per_sm;
     const uint32_t grid = per_block ? static_cast<uint32_t>(n_units)
                                     : static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(resident, n_units)));
@@ -321,9 +330,9 @@ void rng_server_opts_default(rng_server_opts *o) {
   o->hbm_budget_bytes = uint64_t(64) << 30;
   o->step_bytes = uint64_t(2) << 30;
   o->max_steps_in_flight = 2;
-  o->values_per_thread = 8;
+  o->values_per_thread = 4;
   o->max_units_per_step = 1u << 20;
-  o->mode = 2;
+  o->mode = 1;
   o->device = -1;
   o->stream = nullptr;
 }
@@ -338,7 +347,7 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
       return rngi::fail(err, RNG_EINVAL, "rng_server_create: opts.struct_size mismatch");
     o = *opts;
   }
-  if (o.values_per_thread == 0) o.values_per_thread = 8;
+  if (o.values_per_thread == 0) o.values_per_thread = 4;
   if (!rngi::batch_vpt_supported(o.values_per_thread))
     return rngi::fail(err, RNG_EINVAL,
                       "rng_server_create: values_per_thread must be one of 1, 2, 4, 6, 8, 12, 16, 24, 32");
@@ -364,6 +373,7 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
     rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "cudaStreamCreate");
     s->own_stream = rc == RNG_OK;
   }
+  if (!rc) rc = rngi::cuda_fail(err, cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking), "cudaStreamCreate");
   if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&s->base, o.hbm_budget_bytes), "cudaMalloc(server arena)");
   if (!rc) s->arena.reset(o.hbm_budget_bytes);
   const uint32_t n_slots = o.max_steps_in_flight + 1;
@@ -375,6 +385,7 @@ int rng_server_create(const rng_server_opts *opts, rng_server **out, rng_err **e
     if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&t.d_units, size_t(o.max_units_per_step) * sizeof(rngi::BatchUnit)), "cudaMalloc");
     if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&t.d_counter, sizeof(uint32_t)), "cudaMalloc");
     if (!rc) rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming), "cudaEventCreate");
+    if (!rc) rc = rngi::cuda_fail(err, cudaEventCreateWithFlags(&t.uploaded, cudaEventDisableTiming), "cudaEventCreate");
     s->slots.push_back(t);
     s->free_slots.push_back(i);
   }
@@ -536,6 +547,7 @@ void rng_server_destroy(rng_server *s) {
   if (s->th.joinable()) s->th.join();
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->upload) cudaStreamSynchronize(s->upload);
   for (auto &kv : s->tickets) delete kv.second;
   for (TableSlot &t : s->slots) {
     cudaFreeHost(t.h_inst);
@@ -544,8 +556,10 @@ void rng_server_destroy(rng_server *s) {
     cudaFree(t.d_units);
     cudaFree(t.d_counter);
     if (t.done) cudaEventDestroy(t.done);
+    if (t.uploaded) cudaEventDestroy(t.uploaded);
   }
   cudaFree(s->base);
+  if (s->upload) cudaStreamDestroy(s->upload);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
   rngi::live_dec();

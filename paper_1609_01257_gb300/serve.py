@@ -22,8 +22,8 @@ from . import _capi as C
 
 class Server:
     def __init__(self, *, hbm_budget_bytes: int = 64 << 30, max_active: int = 1024,
-                 step_bytes: int = 2 << 30, max_steps_in_flight: int = 2, values_per_thread: int = 8,
-                 max_units_per_step: int = 1 << 20, mode: int = 2, stream=None,
+                 step_bytes: int = 2 << 30, max_steps_in_flight: int = 2, values_per_thread: int = 4,
+                 max_units_per_step: int = 1 << 20, mode: int = 1, stream=None,
                  device: Optional[int] = None):
         lib = C.load()
         o = C.RngServerOpts()

@@ -28,11 +28,14 @@ def _full(srv, ticket, n, T):
     return srv.read(ticket, 0, n * T).reshape(T, n)
 
 
-def test_mix_of_sizes_bit_exact():
+@pytest.mark.parametrize("vpt,mode", [(0, 0), (2, 1), (4, 2), (8, 1), (8, 2), (32, 2)])
+def test_mix_of_sizes_bit_exact(vpt, mode):
+    # (0, 0): the defaults (4 values per thread, one unit per block).
     rs = np.random.default_rng(3)
     reqs = [(int(rs.integers(0, 2**63)), int(rs.integers(1, 70_000)), int(rs.integers(1, 40))) for _ in range(60)]
     reqs += [(5, 1, 1), (6, 2, 3), (7, 257, 1), (8, 4096, 17)]
-    with rng.Server(hbm_budget_bytes=2 << 30, step_bytes=4 << 20) as srv:
+    kw = {"values_per_thread": vpt, "mode": mode} if mode else {}
+    with rng.Server(hbm_budget_bytes=2 << 30, step_bytes=4 << 20, **kw) as srv:
         tickets = {srv.submit(s, n, T): (s, n, T) for s, n, T in reqs}
         got = _collect(srv, len(reqs))
         for t, (s, n, T) in tickets.items():
