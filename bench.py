@@ -1176,7 +1176,8 @@ def run_queue_chart(args):
 
 def run_sweep(args):
     """Roofline sweep: streams 2^16..2^28 (powers of 4) x values per thread
-    1..64, full-write mode and generate-and-checksum mode.
+    1..64 (register stores) and 4, 8, 16 (bulk copies, store_policy 2),
+    full-write mode and generate-and-checksum mode.
 
     Full-write mode: output goes to a ring of two 2 GiB device buffers; each
     launch writes the whole 4 GiB ring once (iterations = ring rows, no row
@@ -1216,6 +1217,7 @@ def run_sweep(args):
 
         for vpt in args.sweep_vpts:
             res[vpt], res_dram[vpt], _ = point(values_per_thread=vpt)
+        bulk = {vpt: point(values_per_thread=vpt, store_policy=2)[0] for vpt in args.sweep_bulk_vpts}
         dflt, dflt_dram, cfg = point()
         T = max(1, (16 * GIB) // (8 * n))
 
@@ -1252,6 +1254,7 @@ def run_sweep(args):
         _json_line({"sweep_streams": n, "rows_per_launch": rows, "launches": launches,
                     "write_GBps_by_vpt": {str(k): round(v, 1) for k, v in res.items()},
                     "dram_GBps_incl_state_by_vpt": {str(k): round(v, 1) for k, v in res_dram.items()},
+                    "write_GBps_bulk_by_vpt": {str(k): round(v, 1) for k, v in bulk.items()},
                     "default_shape": {"kernel": cfg[3], "vpt": cfg[0], "grid": cfg[2], "GBps": round(dflt, 1),
                                       "dram_GBps_incl_state": round(dflt_dram, 1)},
                     "checksum_iterations": T,
@@ -1280,6 +1283,8 @@ def main(argv=None):
     ap.add_argument("--server-mode", type=int, default=1, help="served: 1 one unit per block, 2 persistent")
     ap.add_argument("--sweep-vpts", type=int, nargs="+", default=[1, 2, 4, 6, 8, 12, 16, 24, 32, 48, 64])
     ap.add_argument("--sweep-checksum-vpts", type=int, nargs="+", default=[1, 2, 4, 8, 16, 32, 64])
+    ap.add_argument("--sweep-bulk-vpts", type=int, nargs="+", default=[4, 8, 16],
+                    help="sweep: values per thread of the bulk-copy row kernel (store_policy 2)")
     ap.add_argument("--skip-streams", type=int, nargs="+", default=[1 << 22, 1 << 26, 1 << 28],
                     help="skip: stream counts")
     ap.add_argument("--consumers", type=int, nargs="+", default=[1, 2, 4, 8, 16],
