@@ -315,8 +315,10 @@ int rng_set_state(rng_gen *g, const uint64_t *host_states, uint64_t position, rn
 int rng_sync(rng_gen *g, rng_err **err);
 /* The compute stream (cudaStream_t) the generator launches on. */
 void *rng_compute_stream(rng_gen *g);
-/* Launch configuration chosen for `streams`: values per thread, threads
- * per block and blocks of the grid. */
+/* Register-store launch configuration chosen for `streams` at creation:
+ * values per thread, threads per block and blocks of the grid.  A device
+ * output may run the bulk-copy row kernel in another shape instead (see
+ * store_policy); rng_last_launch reports what a launch ran. */
 int rng_launch_config(const rng_gen *g, uint32_t *values_per_thread,
                       uint32_t *block_threads, uint32_t *grid_blocks);
 

@@ -117,6 +117,8 @@ class Generator:
         return torch.cuda.ExternalStream(self._lib.rng_compute_stream(self._h), device=self.device)
 
     def launch_config(self):
+        """Register-store shape chosen at creation (values per thread, block,
+        grid); ``last_launch()`` reports the kernel a launch actually ran."""
         v, b, g = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         self._lib.rng_launch_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(g))
         return v.value, b.value, g.value
