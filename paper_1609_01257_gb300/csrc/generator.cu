@@ -189,7 +189,10 @@ int gen_launch_rows(rng_gen *g, rngi::RowsLaunch &a, const rngi::LaunchShape &sh
   a.state_out = a.state;
   a.out_mode = g->opts.output_mode;
   rngi::LaunchShape base = shape;
-  if (!device_out) base.bulk_lined = base.bulk_ragged = rngi::BulkChoice{};
+  if (!device_out) {
+    base.bulk_auto = false;
+    base.bulk_forced = rngi::BulkChoice{};
+  }
   const rngi::LaunchShape sh = rngi::resolve_shape(base, a);
   bool swap = false;
   if (!a.ring_rows && a.out && a.s_begin == 0 && a.s_end == g->n) {

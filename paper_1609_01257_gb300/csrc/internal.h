@@ -82,10 +82,10 @@ struct LaunchShape {
   uint32_t grid;
   uint32_t width;         // widest store in values (1, 2, 4) the shape may use
   bool staged = false;    // rows off the 128-byte lines: the staged row kernel
-  BulkChoice bulk_lined;  // bulk-copy kernel for outputs whose rows start on 128-byte lines
-  BulkChoice bulk_ragged; // ... and for the others
-  bool bulk_always = false; // store_policy 2: bulk copies for every device row (else from 128 rows per launch)
-  uint32_t bulk_nb = 0;   // set by resolve_shape: this launch runs the bulk kernel (vpt values per thread)
+  bool bulk_auto = false;  // resolve_shape may pick the bulk-copy kernel for each launch
+  BulkChoice bulk_forced;  // store_policy 2: this bulk-copy shape for every device row
+  uint32_t sms = 0;        // SMs of the device the shape is for
+  uint32_t bulk_nb = 0;    // set by resolve_shape: this launch runs the bulk kernel (vpt values per thread)
 };
 
 // What one row-kernel launch ran (rng_launch_info without struct_size).

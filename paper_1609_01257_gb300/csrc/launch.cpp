@@ -84,28 +84,40 @@ uint32_t bulk_buffers(uint32_t vpt) {
   }
 }
 
-// Bulk-copy row kernel (values per thread, row buffers) chosen when the
-// caller leaves the shape to the library, for rows on 128-byte lines
-// (`lined`) and off them.  Measured on GB300 (1024 rows, GB/s; the register-
+// Bulk-copy row kernel (values per thread, row buffers) for one launch of
+// `rows` rows over `streams` streams when the caller leaves the shape to the
+// library, for rows on 128-byte lines (`lined`) and off them; nb == 0: keep
+// the register or staged kernel.  Measured on GB300 (GB/s; the register-
 // store or staged kernel in brackets):
-//  - on the lines: 2^22 streams 7517 at (8, 12) [7470]; below 3.5 M streams
-//    the register kernels stay ahead (2^20: 7211 [7247]; 2^16: 6574 [6858]);
-//  - off the lines at (8, 12): 2^22 + 1 streams 7125 [6957], an output one
-//    word off a line 7147 [6893], 3,000,017 streams 6983 [6713], 250,001
-//    7078 [5629], 65,537 (banded) 6343 [4957]; at (16, 4): 1,000,003
-//    streams 6769 [6333] (6565 at (8, 12)).
+//  - on the lines, 1024 rows: 2^22 streams 7517 at (8, 12) [7470]; below
+//    3.5 M streams the register kernels stay ahead (2^20: 7211 [7247]; 2^16:
+//    6574 [6858]);
+//  - off the lines, 1024 rows, at (8, 12): 2^22 + 1 streams 7125 [6957], an
+//    output one word off a line 7147 [6893], 3,000,017 streams 6983 [6713],
+//    250,001 7078 [5629], 65,537 (banded) 6343 [4957]; at (16, 4): 1,000,003
+//    streams 6769 [6333] (6565 at (8, 12));
+//  - off the lines, 16-128 rows: 3,000,017 streams at (8, 12) 6215-7121
+//    [6002-7107]; 250,001 streams 2917-6296 [2595-6250]; 65,537 streams
+//    (33 tiles of 2048) at (4, 8) 877-2312 [585-1730]; 1,000,003 streams
+//    staged stays level or ahead below 128 rows (6248-6494 at 64-96 rows
+//    against 6155-6443); at 8 rows every form is within ~10 %.
 // Each copy has a fixed cost: 4 KiB copies (two values per thread) stayed
 // near 4.2 TB/s, so bulk tiles hold 8 KiB and more.  With one block per SM
 // (the buffers take most of its shared memory) each tile's start -- loading
-// its states -- is exposed, so launches of few rows keep the register
+// its states -- is exposed, so lined launches of few rows keep the register
 // kernels: 2^22 streams x 128 rows 7221 [7209], 2^24 x 32 rows 6574 [6580],
 // 2^26 x 8 rows 4852 [5368], 2^28 x 2 rows 2233 [3503].
-constexpr uint64_t kBulkMinRows = 128;
-BulkChoice bulk_default(uint64_t streams, bool lined) {
+BulkChoice bulk_default(uint64_t streams, uint64_t rows, bool lined, uint32_t sms) {
   const uint64_t M = uint64_t(1) << 20;
-  if (lined) return streams >= 7 * M / 2 ? BulkChoice{8, 12} : BulkChoice{};
-  if (streams < 64 * 1024) return BulkChoice{};
-  if (streams >= M / 2 && streams < 2 * M) return BulkChoice{16, 4};
+  if (lined) return streams >= 7 * M / 2 && rows >= 128 ? BulkChoice{8, 12} : BulkChoice{};
+  if (streams < 64 * 1024 || rows < 16) return BulkChoice{};
+  if (streams >= M / 2 && streams < 2 * M) return rows >= 128 ? BulkChoice{16, 4} : BulkChoice{};
+  if (streams < M / 2 && rows < 256) {
+    // Unbanded (banding starts at 256 rows): few tiles of 2048 streams leave
+    // most SMs idle, tiles of 1024 twice fewer.
+    const uint64_t tiles8 = (streams + uint64_t(kGenBlock) * 8 - 1) / (uint64_t(kGenBlock) * 8);
+    if (tiles8 * 2 < sms) return BulkChoice{4, 8};
+  }
   return BulkChoice{8, 12};
 }
 
@@ -117,19 +129,16 @@ LaunchShape rows_shape(uint64_t streams, uint32_t vpt, uint32_t block, int devic
   if (policy == kStoreBulk) {
     // Every row written by bulk copies, whatever its alignment.
     sh.vpt = vpt ? vpt : 8;
-    sh.bulk_lined = sh.bulk_ragged = BulkChoice{sh.vpt, bulk_buffers(sh.vpt)};
-    sh.bulk_always = true;
+    sh.bulk_forced = BulkChoice{sh.vpt, bulk_buffers(sh.vpt)};
     sh.width = 1;
     const uint64_t tiles = (streams + uint64_t(kGenBlock) * sh.vpt - 1) / (uint64_t(kGenBlock) * sh.vpt);
     uint64_t grid = max_grid && max_grid < tiles ? max_grid : tiles;
     if (grid > 0x7fffffffull) grid = 0x7fffffffull;
-    sh.grid = sh.bulk_lined.nb && sh.block == kGenBlock ? static_cast<uint32_t>(grid ? grid : 1) : 0;
+    sh.grid = sh.bulk_forced.nb && sh.block == kGenBlock ? static_cast<uint32_t>(grid ? grid : 1) : 0;
     return sh;
   }
-  if (policy == kStoreStreaming && vpt == 0 && sh.block == kGenBlock && max_grid == 0 && width == 0) {
-    sh.bulk_lined = bulk_default(streams, true);
-    sh.bulk_ragged = bulk_default(streams, false);
-  }
+  sh.bulk_auto = policy == kStoreStreaming && vpt == 0 && sh.block == kGenBlock && max_grid == 0 && width == 0;
+  sh.sms = static_cast<uint32_t>(sms);
   if (sh.block == kGenBlock && streams % 16 != 0) {
     const uint32_t v = staged_vpt(streams, vpt, sms);
     if (v) {
@@ -174,8 +183,10 @@ LaunchShape resolve_shape(const LaunchShape &sh, const RowsLaunch &a) {
   r.bulk_nb = 0;
   if (!a.out) return r;
   const bool lined = a.pitch % 16 == 0 && reinterpret_cast<uintptr_t>(a.out) % 128 == 0;
-  const BulkChoice c = lined ? sh.bulk_lined : sh.bulk_ragged;
-  if (!c.nb || (!sh.bulk_always && a.rows < kBulkMinRows)) return r;
+  const BulkChoice c = sh.bulk_forced.nb ? sh.bulk_forced
+                       : sh.bulk_auto    ? bulk_default(a.s_end - a.s_begin, a.rows, lined, sh.sms)
+                                         : BulkChoice{};
+  if (!c.nb) return r;
   r.vpt = c.vpt;
   r.bulk_nb = c.nb;
   r.staged = false;

@@ -126,3 +126,12 @@ def test_host_destinations_keep_register_stores(host_path):
     g.close()
     assert info["kernel"] != "bulk"
     assert np.array_equal(host.numpy().view(np.uint64), oracle.generate(n, 9, T))
+
+
+def test_last_launch_before_any_launch_is_a_state_error():
+    g = rng.Generator(1000, 1)
+    with pytest.raises(rng.RngError):
+        g.last_launch()
+    g.generate(2)
+    assert g.last_launch()["kernel"] in ("register", "staged", "bulk")
+    g.close()
