@@ -135,3 +135,14 @@ def test_last_launch_before_any_launch_is_a_state_error():
     g.generate(2)
     assert g.last_launch()["kernel"] in ("register", "staged", "bulk")
     g.close()
+
+
+@pytest.mark.parametrize("off", [123_456, (1 << 32) - 4097])
+def test_bulk_copies_with_a_stream_offset(off):
+    # A shard of a larger generator: ids off .. off + n - 1, up to the
+    # 32-bit id limit.
+    n, T = 4097, 9
+    g = rng.Generator(n, 77, stream_offset=off, store_policy=2)
+    a = g.generate(T).cpu().numpy()
+    g.close()
+    assert np.array_equal(a, oracle.generate(n, 77, T, g0=off))

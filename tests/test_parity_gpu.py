@@ -107,19 +107,23 @@ def test_ids_up_to_the_32_bit_limit():
         rng.Generator(n, 5, stream_offset=(1 << 32) - n + 1)
 
 
-def test_maximum_stream_count():
+@pytest.mark.parametrize("policy", [1, 2])
+def test_maximum_stream_count(policy):
     # 2^32 streams (the id width): 2 iterations = 64 GiB of output plus a
-    # 32 GiB state array; sampled values one by one.
+    # 32 GiB state array; sampled values one by one.  Policy 2 runs the
+    # bulk-copy row kernel (2^21 blocks, 64-bit row offsets).
     n, T, seed = 1 << 32, 2, 3
-    g = rng.Generator(n, seed)
+    g = rng.Generator(n, seed, store_policy=policy)
     out = g.generate(T)
     g.sync()
     o64 = out.view(torch.int64).view(-1)
     rs = np.random.default_rng(4)
     idx = [0, 1, n - 1, n, 2 * n - 1] + [int(i) for i in rs.integers(0, 2 * n, 40)]
     vals = o64[torch.tensor(idx, device="cuda")].cpu().numpy().view(np.uint64)
+    ran = g.last_launch()["kernel"]
     del out, o64
     g.close()
+    assert ran == ("bulk" if policy == 2 else "register")
     for k, v in zip(idx, vals):
         i, gg = divmod(k, n)
         assert int(v) == oracle.value(gg, seed, i), (i, gg)
