@@ -113,8 +113,8 @@ BulkChoice bulk_default(uint64_t streams, uint64_t rows, bool lined, uint32_t sm
   if (streams < 64 * 1024 || rows < 16) return BulkChoice{};
   if (streams >= M / 2 && streams < 2 * M) return rows >= 128 ? BulkChoice{16, 4} : BulkChoice{};
   if (streams < M / 2 && rows < 256) {
-    // Unbanded (banding starts at 256 rows): few tiles of 2048 streams leave
-    // most SMs idle, tiles of 1024 twice fewer.
+    // Unbanded (banding starts at 256 rows): when tiles of 2048 streams
+    // would leave most SMs idle, tiles of 1024 give twice as many blocks.
     const uint64_t tiles8 = (streams + uint64_t(kGenBlock) * 8 - 1) / (uint64_t(kGenBlock) * 8);
     if (tiles8 * 2 < sms) return BulkChoice{4, 8};
   }
