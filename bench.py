@@ -697,10 +697,19 @@ def batched_leg(args, clocks=None, write_ceiling=None):
     import paper_1609_01257_gb300 as rng
     import workloads
 
-    inst = workloads.batched_instances(cap_bytes=int(args.batch_cap_gib * GIB))
+    if args.batch_uniform:
+        # A uniform batch instead of the drawn mix: `count` instances of
+        # `streams` x `iterations`, seeds 0 .. count-1.
+        n_u, t_u, k_u = args.batch_uniform
+        inst = [workloads.Instance(streams=n_u, iterations=t_u, seed=k) for k in range(k_u)]
+        name = f"batched: {k_u} instances of {n_u} streams x {t_u} iterations, seeds 0..{k_u - 1}, one CUDA-graph launch"
+    else:
+        inst = workloads.batched_instances(cap_bytes=int(args.batch_cap_gib * GIB))
+        name = BATCHED_NAME.format(cap=args.batch_cap_gib)
     total = sum(i.nbytes for i in inst)
     b = rng.Batch([i.streams for i in inst], [i.iterations for i in inst], [i.seed for i in inst],
-                  values_per_thread=args.batch_vpt, mode=args.batch_mode)
+                  values_per_thread=args.batch_vpt, mode=args.batch_mode,
+                  stores=args.batch_stores)
     cfg = b.config()
     s = b.stream
     for _ in range(args.warmup):
@@ -738,7 +747,7 @@ def batched_leg(args, clocks=None, write_ceiling=None):
     for g in gens:
         g.close()
     b.close()
-    d = {"config": {"workload": BATCHED_NAME.format(cap=args.batch_cap_gib), "instances": len(inst),
+    d = {"config": {"workload": name, "instances": len(inst),
                     "bytes_per_step": total, "tuned": cfg,
                     "l2": f"output {total / GIB:.1f} GiB per step > L2: no flush needed"},
          "value": total / batched_s / 1e9, "unit": "GB/s", "ms_per_step": batched_s * 1e3,
@@ -1277,6 +1286,10 @@ def main(argv=None):
     ap.add_argument("--batch-cap-gib", type=float, default=8.0, help="batched: total output cap")
     ap.add_argument("--batch-vpt", type=int, default=0, help="batched: values per thread (0 = autotune)")
     ap.add_argument("--batch-mode", type=int, default=0, help="batched: 0 autotune, 1 per block, 2 persistent")
+    ap.add_argument("--batch-uniform", type=int, nargs=3, metavar=("STREAMS", "ITERATIONS", "COUNT"),
+                    help="batched: COUNT instances of STREAMS x ITERATIONS instead of the drawn 512-instance mix")
+    ap.add_argument("--batch-stores", type=int, default=0,
+                    help="batched: 0 autotune, 1 register/staged stores, 2 bulk copies for units of 16+ rows")
     ap.add_argument("--step-bytes", type=int, default=2 << 30, help="served: output bytes per step")
     ap.add_argument("--steps-in-flight", type=int, default=2, help="served: launched, unfinished steps")
     ap.add_argument("--server-vpt", type=int, default=4, help="served: values per thread")

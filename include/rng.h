@@ -443,6 +443,11 @@ typedef struct rng_batch_opts {
                                     1 = one work unit per block (the hardware
                                     hands units out in order), 2 = persistent
                                     blocks taking units from a device counter */
+    uint32_t stores;             /* 0 = autotune (both), 1 = register and
+                                    staged stores, 2 = units of at least 16
+                                    rows staged in shared memory and written
+                                    by TMA bulk copies (shorter units keep the
+                                    stores of 1; 0, 4 or 8 values per thread) */
 } rng_batch_opts;
 
 void rng_batch_opts_default(rng_batch_opts *opts);
@@ -467,6 +472,10 @@ int rng_batch_sync(rng_batch *b, rng_err **err);
 int rng_batch_config(const rng_batch *b, uint32_t *values_per_thread,
                      uint32_t *block_threads, uint32_t *grid_blocks,
                      uint64_t *work_units, uint32_t *mode, double *tuned_ms);
+/* Store path the batch runs: *stores = 1 (register and staged stores) or 2
+ * (bulk copies for units of at least 16 rows, from *row_buffers shared row
+ * buffers per block). */
+int rng_batch_stores(const rng_batch *b, uint32_t *stores, uint32_t *row_buffers);
 void *rng_batch_stream(rng_batch *b);
 void rng_batch_destroy(rng_batch *b);
 

@@ -80,6 +80,7 @@ class RngBatchOpts(ctypes.Structure):
         ("stream", c_vp),
         ("device", c_i32),
         ("mode", c_u32),
+        ("stores", c_u32),
     ]
 
 
@@ -160,6 +161,7 @@ SIGNATURES = {
                           ctypes.POINTER(c_vp), P_err], c_int),
     "rng_batch_run": ([c_vp, P_err], c_int),
     "rng_batch_sync": ([c_vp, P_err], c_int),
+    "rng_batch_stores": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)], c_int),
     "rng_batch_config": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32), ctypes.POINTER(c_u32),
                           P_u64, ctypes.POINTER(c_u32), ctypes.POINTER(c_dbl)], c_int),
     "rng_batch_stream": ([c_vp], c_vp),

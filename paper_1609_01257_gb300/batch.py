@@ -13,11 +13,14 @@ class Batch:
     """Instances ``(streams[k], iterations[k], seeds[k])``; ``outputs[k]`` is a
     ``(iterations[k], streams[k])`` uint64 CUDA tensor (iteration-major) that
     every ``run()`` fills with iterations 0 .. iterations[k]-1.  Launch shape
-    is autotuned over values-per-thread unless ``values_per_thread`` is set."""
+    is autotuned over values-per-thread, work distribution (``mode``) and
+    store path (``stores``: 1 register and staged stores, 2 TMA bulk copies
+    for units of 16+ rows) unless fixed."""
 
     def __init__(self, streams: Sequence[int], iterations: Sequence[int], seeds: Sequence[int], *,
                  outputs: Optional[List[torch.Tensor]] = None, values_per_thread: int = 0,
-                 tune_reps: int = 3, mode: int = 0, stream=None, device: Optional[int] = None):
+                 tune_reps: int = 3, mode: int = 0, stores: int = 0, stream=None,
+                 device: Optional[int] = None):
         lib = C.load()
         k = len(streams)
         assert len(iterations) == k and len(seeds) == k and k > 0
@@ -33,6 +36,7 @@ class Batch:
         o.values_per_thread = values_per_thread
         o.tune_reps = tune_reps
         o.mode = mode
+        o.stores = stores
         if stream is None:
             stream = torch.cuda.Stream(device=self.device)  # pooled by torch, never destroyed
         self._torch_stream = stream
@@ -62,8 +66,11 @@ class Batch:
         u, ms, m = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint32()
         self._lib.rng_batch_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(g), ctypes.byref(u),
                                    ctypes.byref(m), ctypes.byref(ms))
+        st, nb = ctypes.c_uint32(), ctypes.c_uint32()
+        self._lib.rng_batch_stores(self._h, ctypes.byref(st), ctypes.byref(nb))
         return {"values_per_thread": v.value, "block_threads": b.value, "grid_blocks": g.value,
-                "work_units": u.value, "tuned_ms": ms.value, "one_unit_per_block": m.value == 1}
+                "work_units": u.value, "tuned_ms": ms.value, "one_unit_per_block": m.value == 1,
+                "stores": "bulk" if st.value == 2 else "register", "row_buffers": nb.value}
 
     def close(self):
         if self._h:

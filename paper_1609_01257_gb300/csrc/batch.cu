@@ -30,6 +30,7 @@ struct rng_batch {
   uint32_t n_units = 0;
   uint32_t vpt = 0, block = 256, grid = 0;
   bool per_block = false;  // one unit per block (no counter) instead of a persistent grid
+  uint32_t bulk_nb = 0;    // > 0: units of 16+ rows written by bulk copies from this many row buffers
   double tuned_ms = 0.0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -46,8 +47,13 @@ void drop_graph(rng_batch *b) {
   b->graph = nullptr;
 }
 
-// Builds the unit table for `vpt`, uploads it and captures the graph.
-int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
+// Row buffers of the bulk-copy batched kernel for `vpt` values per thread
+// when the caller fixes the shape.
+uint32_t default_bulk_buffers(uint32_t vpt) { return vpt == 4 ? 8u : vpt == 8 ? 12u : 0u; }
+
+// Builds the unit table for `vpt`, uploads it and captures the graph
+// (bulk_nb > 0: the bulk-copy variant).
+int prepare(rng_batch *b, uint32_t vpt, bool per_block, uint32_t bulk_nb, rng_err **err) {
   const uint64_t tile = uint64_t(kBlock) * vpt;
   // One tile per unit.  (Grouping the tiles of few-row instances into units
   // of ~1 MiB was measured slower: 6.27 vs 6.61 TB/s on the 512-instance
@@ -94,7 +100,8 @@ int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
   b->n_units = static_cast<uint32_t>(units.size());
   b->vpt = vpt;
   b->block = kBlock;
-  const int per_sm = rngi::batch_work_blocks_per_sm(vpt);
+  b->bulk_nb = bulk_nb;
+  const int per_sm = rngi::batch_work_blocks_per_sm(vpt, bulk_nb);
   const uint64_t resident = uint64_t(rngi::device_sm_count(b->device)) * (per_sm > 0 ? per_sm : 1);
   b->per_block = per_block;
   b->grid = per_block ? b->n_units
@@ -105,7 +112,7 @@ int prepare(rng_batch *b, uint32_t vpt, bool per_block, rng_err **err) {
   if (st == cudaSuccess) {
     cudaError_t s1 = per_block ? cudaSuccess : cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), b->stream);
     cudaError_t s2 = rngi::launch_batch_work(b->d_work, b->n_units, per_block ? nullptr : b->d_counter, vpt,
-                                             b->grid, b->stream);
+                                             b->grid, b->stream, bulk_nb);
     st = cudaStreamEndCapture(b->stream, &b->graph);
     if (st == cudaSuccess) st = s1 != cudaSuccess ? s1 : s2;
   }
@@ -133,6 +140,7 @@ void rng_batch_opts_default(rng_batch_opts *o) {
   o->stream = nullptr;
   o->device = -1;
   o->mode = 0;
+  o->stores = 0;
 }
 
 int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *iterations,
@@ -154,6 +162,9 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     return rngi::fail(err, RNG_EINVAL,
                       "rng_batch_create: values_per_thread must be 0 or one of 1, 2, 4, 6, 8, 12, 16, 24, 32");
   if (o.mode > 2) return rngi::fail(err, RNG_EINVAL, "rng_batch_create: mode must be 0, 1 or 2");
+  if (o.stores > 2) return rngi::fail(err, RNG_EINVAL, "rng_batch_create: stores must be 0, 1 or 2");
+  if (o.stores == 2 && v && !default_bulk_buffers(v))
+    return rngi::fail(err, RNG_EINVAL, "rng_batch_create: stores 2 (bulk copies) runs 0, 4 or 8 values per thread");
   if (o.block_threads && o.block_threads != kBlock)
     return rngi::fail(err, RNG_EINVAL, "rng_batch_create: block_threads must be 0 or 256");
   for (uint32_t k = 0; k < count; ++k) {
@@ -193,23 +204,31 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
     b->own_stream = rc == RNG_OK;
   }
   if (!rc) rc = rngi::cuda_fail(err, cudaMalloc(&b->d_counter, sizeof(uint32_t)), "cudaMalloc(batch counter)");
-  if (!rc && v) rc = prepare(b, v, o.mode == 1, err);
+  if (!rc && v) rc = prepare(b, v, o.mode == 1, o.stores == 2 ? default_bulk_buffers(v) : 0u, err);
   if (!rc && !v) {
     // Autotune: time each candidate's graph and keep the fastest.
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     rc = rngi::cuda_fail(err, cudaEventCreate(&e0), "cudaEventCreate");
     if (!rc) rc = rngi::cuda_fail(err, cudaEventCreate(&e1), "cudaEventCreate");
     const uint32_t reps = o.tune_reps ? o.tune_reps : 3;
-    uint32_t best_v = 0;
+    uint32_t best_v = 0, best_nb = 0;
     bool best_pb = false;
     double best_ms = 0.0;
-    for (int k = 0; k < 18 && !rc; ++k) {
-      static const uint32_t cands[] = {1u, 2u, 4u, 6u, 8u, 12u, 16u, 24u, 32u};
-      const uint32_t cand = cands[k % 9];
-      const bool pb = k >= 9;
+    // Register and staged stores at every compiled values-per-thread count,
+    // then the bulk-copy variants, each with both work distributions.
+    struct Cand {
+      uint32_t vpt, nb;
+    };
+    static const Cand cands[] = {{1, 0}, {2, 0}, {4, 0}, {6, 0}, {8, 0}, {12, 0}, {16, 0}, {24, 0}, {32, 0},
+                                 {4, 8}, {8, 6}, {8, 12}};
+    const int n_cands = static_cast<int>(sizeof(cands) / sizeof(cands[0]));
+    for (int k = 0; k < 2 * n_cands && !rc; ++k) {
+      const uint32_t cand = cands[k % n_cands].vpt, nb = cands[k % n_cands].nb;
+      const bool pb = k >= n_cands;
       if (o.mode == 1 && !pb) continue;
       if (o.mode == 2 && pb) continue;
-      rc = prepare(b, cand, pb, err);
+      if ((o.stores == 1 && nb) || (o.stores == 2 && !nb)) continue;
+      rc = prepare(b, cand, pb, nb, err);
       if (!rc) rc = replay(b, err);  // warm-up
       if (!rc) rc = rngi::cuda_fail(err, cudaEventRecord(e0, b->stream), "cudaEventRecord");
       for (uint32_t r = 0; r < reps && !rc; ++r) rc = replay(b, err);
@@ -219,13 +238,14 @@ int rng_batch_create(uint32_t count, const uint64_t *streams, const uint64_t *it
       if (!rc) rc = rngi::cuda_fail(err, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
       if (!rc && (best_v == 0 || ms / reps < best_ms)) {
         best_v = cand;
+        best_nb = nb;
         best_pb = pb;
         best_ms = ms / reps;
       }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (!rc) rc = prepare(b, best_v, best_pb, err);
+    if (!rc) rc = prepare(b, best_v, best_pb, best_nb, err);
     if (!rc) b->tuned_ms = best_ms;
   }
   if (rc) {
@@ -256,6 +276,13 @@ int rng_batch_config(const rng_batch *b, uint32_t *vpt, uint32_t *block, uint32_
   if (grid) *grid = b->grid;
   if (units) *units = b->n_units;
   if (tuned_ms) *tuned_ms = b->tuned_ms;
+  return RNG_OK;
+}
+
+int rng_batch_stores(const rng_batch *b, uint32_t *stores, uint32_t *row_buffers) {
+  if (!b) return RNG_EINVAL;
+  if (stores) *stores = b->bulk_nb ? 2u : 1u;
+  if (row_buffers) *row_buffers = b->bulk_nb;
   return RNG_OK;
 }
 

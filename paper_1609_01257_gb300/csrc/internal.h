@@ -35,6 +35,10 @@ size_t rows_bulk_smem_bytes(uint32_t vpt, uint32_t nb);
 const void *checksum_kernel_fn(uint32_t vpt, bool banded = false, uint32_t out = 0);
 const void *worklist_kernel_fn(uint32_t vpt);
 const void *batch_work_kernel_fn(uint32_t vpt);
+// Batched form with bulk copies for units of at least 16 rows: (4, 8),
+// (8, 6) or (8, 12) values per thread and row buffers; dynamic shared memory
+// rows_bulk_smem_bytes(vpt, nb).
+const void *batch_work_bulk_kernel_fn(uint32_t vpt, uint32_t nb);
 const void *init_kernel_fn();
 const void *jump_kernel_fn();
 const void *copy_kernel_fn();
@@ -170,9 +174,10 @@ static_assert(sizeof(BatchWork) == 64, "BatchWork is one 64-byte record");
 // Batched-form launch over `n` self-contained units (from the hash; no state):
 // one unit per block when counter == nullptr, else persistent blocks taking
 // units from the counter.
+// bulk_nb > 0: the bulk-copy variant with that many row buffers.
 cudaError_t launch_batch_work(const BatchWork *work, uint32_t n, uint32_t *counter, uint32_t vpt, uint32_t grid,
-                              cudaStream_t st);
-int batch_work_blocks_per_sm(uint32_t vpt);
+                              cudaStream_t st, uint32_t bulk_nb = 0);
+int batch_work_blocks_per_sm(uint32_t vpt, uint32_t bulk_nb = 0);
 cudaError_t launch_batch(const BatchInstance *inst, const BatchUnit *units, uint32_t n_units,
                          uint32_t *counter, uint32_t vpt, uint32_t block, uint32_t grid,
                          cudaStream_t st);

@@ -694,6 +694,69 @@ __global__ void __launch_bounds__(kBlock) batch_work_kernel(const BatchWork *__r
   }
 }
 
+// Batched form with the bulk-copy row path: units of at least
+// kBulkUnitRows rows stage each row in one of NB shared buffers and write it
+// with a TMA bulk copy (emit_rows_bulk); shorter units take process_work's
+// stores, with the same dynamic shared memory as their staging buffer once
+// the earlier units' copies have finished reading it.  Every thread of the
+// block calls it.
+constexpr uint64_t kBulkUnitRows = 16;
+
+template <int VPT, int NB>
+__device__ __forceinline__ void process_work_bulk(const BatchWork &w, uint64_t *buf, uint32_t &kb, uint32_t &warm) {
+  if (w.rows < kBulkUnitRows) {
+    if (warm) {
+      if (threadIdx.x == 0) bulk_wait_read<0>();
+      __syncthreads();
+      kb = 0;
+      warm = 0;
+    }
+    process_work<VPT>(w, buf);
+    return;
+  }
+  RowsLaunch a;
+  a.state = nullptr;
+  a.out = w.out;
+  a.pitch = w.streams;
+  a.s_begin = w.s_begin;
+  a.s_end = w.s_begin + w.count;
+  a.id_base = 0;
+  a.rows = w.rows;
+  a.key = w.key;
+  a.from_hash = 1;
+  a.write_state = 0;
+  a.ring_rows = 0;
+  uint64_t st[VPT];
+  load_tile<VPT, 1>(st, a, 0, w.count);
+  emit_rows_bulk<VPT, NB>(st, w.out + w.s_begin, w.streams, w.rows, w.count, 0, buf, kb, warm);
+}
+
+template <int VPT, int NB>
+__global__ void __launch_bounds__(kBlock) batch_work_bulk_kernel(const BatchWork *__restrict__ work, uint32_t n,
+                                                                 uint32_t *counter) {
+  extern __shared__ __align__(128) uint64_t bulk_buf[];
+  static_assert(bulk_words<VPT, NB>() >= staged_words<VPT>(), "short units stage in the bulk buffers");
+  uint32_t kb = 0, warm = 0;
+  if (counter == nullptr) {
+    if (blockIdx.x < n) {
+      const BatchWork w = work[blockIdx.x];
+      process_work_bulk<VPT, NB>(w, bulk_buf, kb, warm);
+    }
+  } else {
+    __shared__ uint32_t s_unit;
+    for (;;) {
+      if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
+      __syncthreads();
+      const uint32_t u = s_unit;
+      __syncthreads();
+      if (u >= n) break;
+      const BatchWork w = work[u];
+      process_work_bulk<VPT, NB>(w, bulk_buf, kb, warm);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
+}
+
 const void *select_batch_work(uint32_t vpt) {
   switch (vpt) {
     case 1: return reinterpret_cast<const void *>(&batch_work_kernel<1>);
@@ -891,6 +954,12 @@ const void *rows_staged_kernel_fn(uint32_t vpt, bool banded, uint32_t out) {
 const void *checksum_kernel_fn(uint32_t vpt, bool banded, uint32_t out) { return select_checksum(vpt, banded, out); }
 const void *worklist_kernel_fn(uint32_t vpt) { return select_batch(vpt); }
 const void *batch_work_kernel_fn(uint32_t vpt) { return select_batch_work(vpt); }
+const void *batch_work_bulk_kernel_fn(uint32_t vpt, uint32_t nb) {
+  if (vpt == 4 && nb == 8) return reinterpret_cast<const void *>(&batch_work_bulk_kernel<4, 8>);
+  if (vpt == 8 && nb == 6) return reinterpret_cast<const void *>(&batch_work_bulk_kernel<8, 6>);
+  if (vpt == 8 && nb == 12) return reinterpret_cast<const void *>(&batch_work_bulk_kernel<8, 12>);
+  return nullptr;
+}
 const void *init_kernel_fn() { return reinterpret_cast<const void *>(&init_kernel); }
 const void *jump_kernel_fn() { return reinterpret_cast<const void *>(&jump_kernel); }
 const void *copy_kernel_fn() { return reinterpret_cast<const void *>(&copy_kernel); }

@@ -457,17 +457,34 @@ int batch_blocks_per_sm(uint32_t vpt, uint32_t block) {
   return fn ? occupancy(fn, block) : 0;
 }
 
-int batch_work_blocks_per_sm(uint32_t vpt) {
+int batch_work_blocks_per_sm(uint32_t vpt, uint32_t bulk_nb) {
+  if (bulk_nb) {
+    const void *fn = batch_work_bulk_kernel_fn(vpt, bulk_nb);
+    if (!fn) return 0;
+    const size_t smem = rows_bulk_smem_bytes(vpt, bulk_nb);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+      return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, static_cast<int>(kGenBlock), smem) != cudaSuccess || n < 1)
+      n = 1;
+    return n;
+  }
   const void *fn = batch_work_kernel_fn(vpt);
   return fn ? occupancy(fn, kGenBlock) : 0;
 }
 
 cudaError_t launch_batch_work(const BatchWork *work, uint32_t n, uint32_t *counter, uint32_t vpt, uint32_t grid,
-                              cudaStream_t st) {
-  const void *fn = batch_work_kernel_fn(vpt);
+                              cudaStream_t st, uint32_t bulk_nb) {
+  const void *fn = bulk_nb ? batch_work_bulk_kernel_fn(vpt, bulk_nb) : batch_work_kernel_fn(vpt);
   if (!fn) return cudaErrorInvalidValue;
+  size_t smem = 0;
+  if (bulk_nb) {
+    smem = rows_bulk_smem_bytes(vpt, bulk_nb);
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
   void *params[] = {&work, &n, &counter};
-  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kGenBlock), params, 0, st);
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kGenBlock), params, smem, st);
   if (e == cudaSuccess) count_launch();
   return e;
 }

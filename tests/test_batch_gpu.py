@@ -33,7 +33,7 @@ def test_replay_is_identical_and_autotuned():
     seeds = [10, 11, 12]
     b = rng.Batch(streams, iters, seeds)
     cfg = b.config()
-    assert cfg["values_per_thread"] in (1, 2, 4, 8, 16, 32) and cfg["tuned_ms"] > 0
+    assert cfg["values_per_thread"] in (1, 2, 4, 6, 8, 12, 16, 24, 32) and cfg["tuned_ms"] > 0
     for o in b.outputs:
         o.view(torch.int64).zero_()
     torch.cuda.synchronize()
@@ -96,6 +96,58 @@ def test_rows_off_the_cache_lines_are_staged(vpt, mode):
         mask[a:e] = False
     assert (host[mask] == 0x5A5A).all()
     b.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("vpt", [4, 8])
+def test_bulk_copies_for_long_units(vpt, mode):
+    # stores = 2: units of 16 or more rows are written by TMA bulk copies,
+    # shorter ones by the register and staged stores, in one kernel (with
+    # persistent blocks a block moves between the two paths).  Odd and even
+    # pitches, outputs off 16-byte and 128-byte boundaries, canaries around
+    # every output.
+    streams = [2049, 4097, 70_001, 1000, 4103, 16, 5000, 1, 300, 65_536]
+    iters = [20, 3, 16, 40, 15, 33, 2, 50, 17, 18]
+    seeds = [3, 1, 4, 1, 5, 9, 2, 6, 5, 3]
+    offsets = [1, 3, 5, 7, 16, 9, 2, 1, 4, 0]
+    total = sum(o + n * t + 3 for o, n, t in zip(offsets, streams, iters))
+    buf = torch.full((total + 16,), 0x5A5A, dtype=torch.int64, device="cuda").view(torch.uint64)
+    outs, spans, pos = [], [], 0
+    for o, n, t in zip(offsets, streams, iters):
+        pos += o
+        outs.append(buf[pos:pos + n * t].view(t, n))
+        spans.append((pos, pos + n * t))
+        pos += n * t + 3
+    b = rng.Batch(streams, iters, seeds, outputs=outs, values_per_thread=vpt, mode=mode, stores=2)
+    cfg = b.config()
+    assert cfg["stores"] == "bulk" and cfg["row_buffers"] > 0
+    for _ in range(2):  # a replay rewrites the same values
+        b.run()
+        b.sync()
+        for k in range(len(streams)):
+            assert np.array_equal(outs[k].cpu().numpy(), oracle.generate(streams[k], seeds[k], iters[k])), k
+    host = buf.view(torch.int64).cpu().numpy()
+    mask = np.ones(host.size, dtype=bool)
+    for a, e in spans:
+        mask[a:e] = False
+    assert (host[mask] == 0x5A5A).all()
+    b.close()
+
+
+def test_autotune_over_both_store_paths():
+    # stores = 0 tunes over register/staged and bulk-copy shapes; stores = 1
+    # keeps the first.  Either way every value matches the oracle.
+    streams, iters, seeds = [70_001, 3000, 257], [40, 20, 5], [7, 8, 9]
+    for stores in (0, 1, 2):
+        b = rng.Batch(streams, iters, seeds, stores=stores)
+        cfg = b.config()
+        if stores:
+            assert cfg["stores"] == ("bulk" if stores == 2 else "register")
+        b.run()
+        b.sync()
+        for k in range(3):
+            assert np.array_equal(b.outputs[k].cpu().numpy(), oracle.generate(streams[k], seeds[k], iters[k]))
+        b.close()
 
 
 def _row_checksums(block):

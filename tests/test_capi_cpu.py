@@ -223,11 +223,18 @@ def test_batch_and_server_options_are_checked_on_the_host(L):
 
     o = C.RngBatchOpts()
     L.rng_batch_opts_default(ctypes.byref(o))
-    for field, bad in [("values_per_thread", 3), ("mode", 3), ("block_threads", 128), ("struct_size", 8)]:
+    for field, bad in [("values_per_thread", 3), ("mode", 3), ("block_threads", 128), ("struct_size", 8),
+                       ("stores", 3)]:
         b = C.RngBatchOpts()
         ctypes.memmove(ctypes.byref(b), ctypes.byref(o), ctypes.sizeof(o))
         setattr(b, field, bad)
         assert batch(b)[0] == C.RNG_EINVAL, field
+    for vpt in (1, 2, 6, 12, 16, 32):  # bulk copies run 4 or 8 values per thread
+        b = C.RngBatchOpts()
+        ctypes.memmove(ctypes.byref(b), ctypes.byref(o), ctypes.sizeof(o))
+        b.stores, b.values_per_thread = 2, vpt
+        rc, msg = batch(b)
+        assert rc == C.RNG_EINVAL and b"stores" in msg, vpt
     assert batch(streams=0)[0] == C.RNG_EINVAL
     assert batch(streams=(1 << 32) + 1)[0] == C.RNG_EINVAL
     assert batch(iterations=0)[0] == C.RNG_EINVAL
