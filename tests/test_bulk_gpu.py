@@ -146,3 +146,18 @@ def test_bulk_copies_with_a_stream_offset(off):
     a = g.generate(T).cpu().numpy()
     g.close()
     assert np.array_equal(a, oracle.generate(n, 77, T, g0=off))
+
+
+@pytest.mark.parametrize("grid", [1, 3, 7])
+@pytest.mark.parametrize("n,T", [(70_001, 9), (20_000, 40), (4096 * 5 + 3, 17)])
+def test_bulk_copies_with_blocks_striding_over_tiles(grid, n, T):
+    # A grid smaller than the tile count: each block runs several tiles one
+    # after another, its row buffers rotating across them.
+    g = rng.Generator(n, 13, store_policy=2, grid_blocks=grid)
+    a = g.generate(T).cpu().numpy()
+    info = g.last_launch()
+    b = g.generate(2).cpu().numpy()
+    g.close()
+    want = oracle.generate(n, 13, T + 2)
+    assert info["kernel"] == "bulk" and info["grid"] == grid
+    assert np.array_equal(a, want[:T]) and np.array_equal(b, want[T:])
